@@ -1,0 +1,209 @@
+"""Oracle preconditioned conjugate gradient and preconditioners (FP64).
+
+PCG (Section 5 remark: the linear systems are solved by preconditioned conjugate gradients), in
+the textbook order of Saad's preconditioned CG:
+    r0 = b - A x0, z0 = P^{-1} r0, p0 = z0
+    for j = 0, 1, ...:
+        w = A p_j;  alpha_j = (r_j, z_j) / (w, p_j)
+        x_{j+1} = x_j + alpha_j p_j;  r_{j+1} = r_j - alpha_j w
+        stop when ||r_{j+1}||_2 <= rtol ||b||_2
+        z_{j+1} = P^{-1} r_{j+1};  beta_j = (r_{j+1}, z_{j+1}) / (r_j, z_j)
+        p_{j+1} = z_{j+1} + beta_j p_j
+At exit the true residual ||b - A x|| / ||b|| is computed; if it exceeds rtol the iteration
+restarts from the true residual (at most max_restarts times). b = 0 returns x = 0.
+
+Preconditioners:
+  Jacobi ("DIAG" of the Section 5 remark, and the labelled fallback): P = diag(A).
+  IC0 (Section 5 remark, for the velocity and mass systems): incomplete Cholesky with zero
+    fill on the pattern of A, in multicolour order (colour = (i&1) | (j&1)<<1 | (k&1)<<2 of the
+    node's grid indices; no stencil edge joins two nodes of one colour) or in natural order.
+    A non-positive pivot retries with A + s diag(A), s = 1e-3 * 2^m, m = 0..10 (shifted IC).
+Pressure (Section 5 remark, zero-mean Lagrange multiplier): the augmented system
+  [K_I m; m' 0][q; lambda] = [b; 0] with m = M 1 gives lambda = 1'b / 1'm; CG solves
+  K_I q = b - lambda m (now consistent) and q is shifted to m'q = 0.
+
+Pins (tests/test_oracle_pcg.py): dense Cholesky and dense augmented solves on small meshes,
+the IC0 defining property (L L^T)_ij = A_ij on the pattern, iteration counts equal to scipy's
+cg with the same preconditioner, A-conjugacy of the search directions.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Callable, List, Optional
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import native
+
+
+@dataclass
+class SolveResult:
+    x: np.ndarray
+    iters: int
+    restarts: int
+    rel_res_true: float
+    rel_res_rec: float
+    converged: bool
+    res_history: List[float] = field(default_factory=list)
+    alphas: List[float] = field(default_factory=list)
+    betas: List[float] = field(default_factory=list)
+
+
+def jacobi_preconditioner(A: sp.csr_matrix) -> Callable[[np.ndarray], np.ndarray]:
+    d = A.diagonal().copy()
+    if np.any(d <= 0):
+        raise ValueError("Jacobi needs a positive diagonal")
+    inv = 1.0 / d
+    return lambda r: inv * r
+
+
+def identity_preconditioner(A=None):
+    return lambda r: r.copy()
+
+
+@dataclass
+class IC0:
+    perm: np.ndarray        # new position -> old index
+    indptr: np.ndarray
+    indices: np.ndarray
+    L: np.ndarray
+    shift: float
+    lower: sp.csr_matrix    # the (shifted) permuted lower triangle that was factored
+
+    def factor_matrix(self) -> sp.csr_matrix:
+        n = len(self.perm)
+        return sp.csr_matrix((self.L, self.indices, self.indptr), shape=(n, n))
+
+    def apply(self, r: np.ndarray) -> np.ndarray:
+        z_perm = native.ic0_solve(self.indptr, self.indices, self.L, r[self.perm])
+        z = np.empty_like(z_perm)
+        z[self.perm] = z_perm
+        return z
+
+
+def multicolour_order(colour: np.ndarray) -> np.ndarray:
+    """Nodes sorted by colour, ties in natural order (a stable sort)."""
+    return np.argsort(colour, kind="stable")
+
+
+def ic0_factor(A: sp.csr_matrix, perm: Optional[np.ndarray] = None, max_shifts: int = 10) -> IC0:
+    n = A.shape[0]
+    perm = np.arange(n) if perm is None else np.asarray(perm)
+    B = A[perm][:, perm].tocsr()
+    B.sort_indices()
+    lower = sp.tril(B, format="csr")
+    lower.sort_indices()
+    diag = B.diagonal()
+    shift = 0.0
+    for m in range(-1, max_shifts + 1):
+        if m >= 0:
+            shift = 1e-3 * 2.0 ** m
+        Lw = lower.copy()
+        if shift:
+            Lw = (Lw + sp.diags(shift * diag)).tocsr()
+            Lw.sort_indices()
+        L, st = native.ic0_factor(Lw.indptr, Lw.indices, Lw.data)
+        if st == 0:
+            return IC0(perm=perm, indptr=Lw.indptr.astype(np.int64), indices=Lw.indices.astype(np.int32),
+                       L=L, shift=shift, lower=Lw)
+    raise ArithmeticError("IC0 breakdown after the shift limit")
+
+
+def ic0_preconditioner(A: sp.csr_matrix, colour: Optional[np.ndarray] = None):
+    perm = multicolour_order(colour) if colour is not None else None
+    f = ic0_factor(A, perm)
+    return f.apply, f
+
+
+def pcg(A, b: np.ndarray, x0: Optional[np.ndarray] = None, rtol: float = 1e-8, max_iter: int = 100000,
+        precond: Optional[Callable] = None, max_restarts: int = 3, record: bool = False) -> SolveResult:
+    n = len(b)
+    precond = precond or identity_preconditioner()
+    bnorm = float(np.sqrt(b @ b))
+    if bnorm == 0.0:
+        return SolveResult(np.zeros(n), 0, 0, 0.0, 0.0, True)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    tol = rtol * bnorm
+    iters = 0
+    restarts = 0
+    hist, alphas, betas = [], [], []
+    while True:
+        r = b - A @ x
+        rnorm = float(np.sqrt(r @ r))
+        converged = rnorm <= tol
+        if not converged:
+            z = precond(r)
+            p = z.copy()
+            rz = float(r @ z)
+            while iters < max_iter:
+                w = A @ p
+                pw = float(p @ w)
+                alpha = rz / pw
+                x += alpha * p
+                r -= alpha * w
+                iters += 1
+                rnorm = float(np.sqrt(r @ r))
+                if record:
+                    hist.append(rnorm)
+                    alphas.append(alpha)
+                if rnorm <= tol:
+                    converged = True
+                    break
+                z = precond(r)
+                rz_new = float(r @ z)
+                beta = rz_new / rz
+                if record:
+                    betas.append(beta)
+                rz = rz_new
+                p = z + beta * p
+        true_res = float(np.linalg.norm(b - A @ x)) / bnorm
+        if true_res <= rtol or restarts >= max_restarts or iters >= max_iter:
+            return SolveResult(x, iters, restarts, true_res, rnorm / bnorm, true_res <= rtol,
+                               hist, alphas, betas)
+        restarts += 1
+
+
+def pressure_solve(K: sp.csr_matrix, m: np.ndarray, b: np.ndarray, x0: Optional[np.ndarray] = None,
+                   rtol: float = 1e-8, max_iter: int = 100000, precond=None, **kw) -> SolveResult:
+    """Mean-zero solution of the pure-Neumann system via the Lagrange-multiplier reading.
+
+    The constraint m'q = 0 is kept on every iterate: x0 is projected onto it and each
+    preconditioned residual z is projected by z <- z - (m'z / 1'm) 1. In exact arithmetic this
+    only shifts the search directions along the null vector 1 (K 1 = 0, 1'r = 0), so alpha,
+    beta and the residuals are those of plain PCG; in floating point it stops the null-space
+    component of the iterate from drifting, which otherwise stalls the true residual.
+    """
+    one_m = m.sum()
+    lam = b.sum() / one_m
+    bc = b - lam * m
+    P = precond or jacobi_preconditioner(K)
+
+    def projected(r):
+        z = P(r)
+        return z - (m @ z) / one_m
+
+    x0p = None if x0 is None else x0 - (m @ x0) / one_m
+    res = pcg(K, bc, x0=x0p, rtol=rtol, max_iter=max_iter, precond=projected, **kw)
+    res.x = res.x - (m @ res.x) / one_m
+    return res
+
+
+# ---- dense references for tiny meshes (pins) --------------------------------------------------
+
+def dense_cholesky_solve(A: sp.spmatrix, b: np.ndarray) -> np.ndarray:
+    import scipy.linalg as sla
+    c = sla.cho_factor(A.toarray(), lower=True)
+    return sla.cho_solve(c, b)
+
+
+def dense_augmented_solve(K: sp.spmatrix, m: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Solve [K m; m' 0][q; lambda] = [b; 0] densely (the Lagrange-multiplier system)."""
+    n = K.shape[0]
+    Aug = np.zeros((n + 1, n + 1))
+    Aug[:n, :n] = K.toarray()
+    Aug[:n, n] = m
+    Aug[n, :n] = m
+    rhs = np.concatenate([b, [0.0]])
+    sol = np.linalg.solve(Aug, rhs)
+    return sol[:n]
