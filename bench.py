@@ -1,0 +1,373 @@
+"""Benchmark: one projection step of the 512 x 512 x 32 synthetic ocean basin in FP64.
+
+A step is one pass of the whole hot path from rest: velocity right-hand side, three velocity
+PCG solves (IC0), divergence right-hand side, the zero-mean pressure PCG (Jacobi / DIAG), the
+pressure update and the lumped velocity correction. The metric is the algorithmic bandwidth of
+the step's PCG iterations (GB/s), reported with its fraction of the measured HBM peak; solves/s
+and latency come along. Operators (about 4.5 GB) exceed the 126 MB L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the only baseline this method has) on a bounded
+window of the same basin, on one host core.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "PCG GB/s % of HBM peak; solves/s, p99 latency vs plain FP64 at 1e-8 residual"
+WORKLOAD = "ocean basin 512x512 columns x 32 sigma layers, one FP64 projection step from rest"
+CPU_WINDOW = 48     # columns per side of the oracle's bounded sample
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---- clocks during the timed region ------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="pm_clocks_", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        try:
+            self.proc.terminate()
+            self.proc.wait(timeout=5)
+        except Exception:
+            pass
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = sorted(float(r[1]) for r in rows)
+        out["sm_mhz"] = sm[len(sm) // 2]
+        out["sm_max_mhz"] = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        out["reasons"] = sorted(reasons)
+        out["samples"] = len(rows)
+        return out
+
+
+# ---- the oracle's bounded sample (CPU baseline and reference arm) ------------------------------
+
+def oracle_window_basin():
+    """A CPU_WINDOW x CPU_WINDOW window of the same synthetic ocean basin (largest component)."""
+    from workloads import ocean_basin
+    from workloads.basins import _keep_largest_cell_component
+    full = ocean_basin()
+    m = full.mask
+    best, bj, bi = -1, 0, 0
+    for j0 in range(0, full.ny - CPU_WINDOW, 32):
+        for i0 in range(0, full.nx - CPU_WINDOW, 32):
+            s = int(m[j0:j0 + CPU_WINDOW, i0:i0 + CPU_WINDOW].sum())
+            if s > best:
+                best, bj, bi = s, j0, i0
+    sl = (slice(bj, bj + CPU_WINDOW), slice(bi, bi + CPU_WINDOW))
+    full.mask = _keep_largest_cell_component(m[sl].copy())
+    full.depth = full.depth[sl].copy()
+    full.coriolis = full.coriolis[sl].copy()
+    full.theta = full.theta[(slice(None),) + sl].copy()
+    full.nx = full.ny = CPU_WINDOW
+    full.name = f"ocean512-window{CPU_WINDOW}x{CPU_WINDOW}x{full.nz}"
+    return full
+
+
+def oracle_step_bytes(n, rep):
+    """Algorithmic PCG bytes of a step, the same per-row model as the GPU path."""
+    per_jac = 15 * 8 + 8 + 8 + 5 * 8 + 2 * 8 + 3 * 8 + 8
+    per_ic0 = per_jac + 2 * 8 * 8 + 4 * 8
+    its_vel = sum(r.iters for r in rep.vel)
+    return n * (its_vel * per_ic0 + rep.pres.iters * per_jac)
+
+
+def cpu_worker(steps: int, warmup: int):
+    """Run the oracle project step on the window; print one JSON line (GB/s, seconds)."""
+    from oracle import fem, step
+    basin = oracle_window_basin()
+    ops = fem.assemble(basin)
+    opts = step.StepOptions(vel_rtol=1e-8, pres_rtol=1e-8)
+    rates, secs = [], []
+    for it in range(warmup + steps):
+        st = step.initial_state(ops.n)
+        t0 = time.perf_counter()
+        rep = step.project_step(ops, st, opts)
+        dt = time.perf_counter() - t0
+        if it >= warmup:
+            rates.append(oracle_step_bytes(ops.n, rep) / dt / 1e9)
+            secs.append(dt)
+    print(json.dumps({"gbs": sum(rates) / len(rates), "seconds": sum(secs) / len(secs), "n": ops.n,
+                      "sample": basin.name, "iters": [r.iters for r in rep.vel] + [rep.pres.iters]}))
+
+
+def run_cpu_oracle(steps: int, warmup: int):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", "--steps", str(steps),
+                        "--warmup", str(warmup)], capture_output=True, text=True, env=env, timeout=3600)
+    if r.returncode != 0:
+        raise RuntimeError("oracle baseline failed:\n" + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# ---- our arm -----------------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1207_0486_gb300 as pm
+    from paper_1207_0486_gb300 import api
+    from workloads import ocean_basin
+
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev_index = torch.cuda.current_device()
+
+    basin = ocean_basin()
+    op = pm.assemble_operator(basin)
+    st = pm.State(op)
+    t1 = torch.from_numpy(op.column_field(basin.theta[0])).cuda()
+    t2 = torch.from_numpy(op.column_field(basin.theta[1])).cuda()
+    vel = pm.Options(rtol=1e-8, prec=pm.PREC_IC0, max_iter=500000)
+    pres = pm.Options(rtol=1e-8, prec=pm.PREC_JACOBI, max_iter=500000)
+
+    def one_step():
+        st.set(step_index=0)
+        return pm.project_step(op, st, t1, t2, vel, pres)
+
+    for _ in range(args.warmup):
+        stats = one_step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(dev_index)
+    clocks.start()
+    time.sleep(0.3)
+    api.kernel_timing(True)
+    launches0 = pm.kernel_launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    all_stats = []
+    for _ in range(args.steps):
+        all_stats.append(one_step())
+    e1.record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = pm.kernel_launch_count() - launches0
+    ms_total = e0.elapsed_time(e1)
+    kt = {k: api.kernel_timing_get(k) for k in (api.KT_SPMV, api.KT_UPDATE, api.KT_PUPDATE, api.KT_IC0)}
+    api.kernel_timing(False)
+    clk = clocks.stop()
+
+    bytes_step = sum(sum(s.bytes_moved for s in stats[:4]) for stats in all_stats) / args.steps
+    solves_step = 4
+    ms_step = ms_total / args.steps
+    if dist:
+        t = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * bytes_step / (ms_step * 1e-3) / 1e9
+
+    # roofline of the dominant kernel class, timed live with events on the solve stream
+    n = op.n
+    per_launch_bytes = {
+        api.KT_SPMV: n * (15 * 8 + 8 + 8),            # values, p (gathers cached), w
+        api.KT_UPDATE: n * (4 * 8 + 2 * 8),           # IC0 path: x, r, p, w read; x, r written
+        api.KT_PUPDATE: n * (3 * 8 + 8) / 2,          # (r, z) dot + p update, two launches
+        api.KT_IC0: n * (2 * 8 * 8 + 4 * 8) / 16,     # F (8 per row per sweep), r/y/z, per launch
+    }
+    names = {api.KT_SPMV: "k_cg_spmv", api.KT_UPDATE: "k_cg_update", api.KT_PUPDATE: "k_cg_rho+k_cg_pupd",
+             api.KT_IC0: "k_ic0_sweep"}
+    dom = max(kt, key=lambda k: kt[k][0])
+    dom_ms, dom_launches = kt[dom]
+    peak, peak_kind = measured_peaks()
+    avg_s = dom_ms * 1e-3 / max(dom_launches, 1)
+    achieved = per_launch_bytes[dom] / avg_s / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        try:
+            with open(prof) as fh:
+                traffic = json.load(fh).get(names[dom])
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "kernel": names[dom], "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": peak_kind,
+                "kernel_share_of_step": round(dom_ms / max(ms_total, 1e-9), 4),
+                "classes_ms_per_step": {names[k]: round(v[0] / args.steps, 3) for k, v in kt.items()}}
+
+    # end to end through the C ABI with host buffers: theta in, (u1, u2, u3, p) out each step
+    e2e = None
+    if not args.no_e2e:
+        th_h = [torch.from_numpy(op.column_field(basin.theta[c])).pin_memory() for c in range(2)]
+        outs_h = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(4)]
+        th_d = [torch.empty(op.ncols, dtype=torch.float64, device="cuda") for _ in range(2)]
+        k_e2e = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record()
+        e2e_bytes = 0.0
+        for _ in range(k_e2e):
+            for c in range(2):
+                th_d[c].copy_(th_h[c], non_blocking=True)
+            st.set(step_index=0)
+            s_e = pm.project_step(op, st, th_d[0], th_d[1], vel, pres)
+            e2e_bytes += sum(s.bytes_moved for s in s_e[:4])
+            for h, d in zip(outs_h, st.get()):
+                h.copy_(d, non_blocking=True)
+        f1.record()
+        torch.cuda.synchronize()
+        ms_e2e = f0.elapsed_time(f1) / k_e2e
+        if dist:
+            t = torch.tensor([ms_e2e], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e2e = float(t.item())
+        e2e = {"value": round(world * (e2e_bytes / k_e2e) / (ms_e2e * 1e-3) / 1e9, 2), "unit": "GB/s",
+               "h2d_bytes_per_step": 2 * op.ncols * 8, "d2h_bytes_per_step": 4 * n * 8,
+               "ms_per_step": round(ms_e2e, 3)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            w = run_cpu_oracle(1, 0)
+            cpu = {"value": round(w["gbs"], 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                   "sample": f"one oracle projection step (FP64, IC0 velocity, Jacobi pressure, rtol 1e-8) "
+                             f"on {w['sample']} ({w['n']} nodes), {w['seconds']:.1f} s",
+                   "seconds_per_step": round(w["seconds"], 2)}
+        except Exception as ex:  # the GPU number stands on its own
+            cpu = {"value": None, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"[:200]}
+
+    last = all_stats[-1]
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded ocean basin: smoothed-noise land mask, sum-of-Gaussians bathymetry)",
+            "config": {"workload": WORKLOAD, "basin": basin.name, "nodes": n, "columns": op.ncols,
+                       "velocity": "IC0-PCG x3 (multicolour), rtol 1e-8",
+                       "pressure": "Jacobi(DIAG)-PCG, zero-mean multiplier, rtol 1e-8",
+                       "correction": "lumped mass", "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "operators 4.5 GB > L2, no flush needed"},
+            "pct_hbm_peak": round(value / world / peak, 4),
+            "solves_per_s": round(world * solves_step / (ms_step * 1e-3), 3),
+            "iters": [int(s.iters) for s in last[:4]],
+            "rel_residual_true": [float(f"{s.rel_residual_true:.3e}") for s in last[:4]],
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return
+    w = run_cpu_oracle(args.steps, args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(w["gbs"], 4), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(w["seconds"] * 1e3, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": w["sample"]},
+        "cpu_baseline": {"value": round(w["gbs"], 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"each step: one oracle projection step on {w['sample']} ({w['n']} nodes)"},
+        "e2e": {"value": round(w["gbs"], 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-worker", action="store_true")
+    args = ap.parse_args()
+    if args.cpu_worker:
+        cpu_worker(args.steps, args.warmup)
+        return
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

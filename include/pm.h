@@ -1,0 +1,224 @@
+/* pm.h -- C ABI of the GB300 projection-method FEM solver library (libpm_gb300.so).
+ *
+ * The library implements the per-time-step linear algebra of a BDF2 velocity-correction
+ * projection method for the anisotropic Navier-Stokes equations in a thin layered basin
+ * (Besson & Straubhaar, "Wind driven 3D Navier-Stokes circulation in the Atlantic"):
+ *   - P1 finite element operators on a layered (sigma) grid whose hexes are split into six
+ *     Kuhn tetrahedra (Section 5, Eqs. fofa_velo_pred_h .. fofa_velo_cor_h);
+ *   - preconditioned conjugate gradient solves of the velocity prediction and pressure
+ *     increment systems (Section 5 remark, items 1-3);
+ *   - the projection step itself (Section 3, Eqs. pred_velo .. press_cor_cl).
+ *
+ * Conventions shared by every entry point:
+ *   - Status: every int-returning call returns a PM_* status code; nothing throws or exits.
+ *     pm_last_error() gives a one-line message for the calling thread's last failure.
+ *   - Node order: ocean columns in row-major (j, i) order of the grid, and node id =
+ *     column * nz + k, k = 0 at the sea floor and k = nz-1 at the surface. pm_operator_columns()
+ *     returns the (i, j) of each column.
+ *   - Device vectors: caller-owned device pointers to contiguous FP64 arrays of length n (or
+ *     ncols for per-column surface fields) in that node order. The library never frees them.
+ *   - Streams: all GPU work of a call is enqueued on the given stream (a cudaStream_t; NULL =
+ *     legacy default stream). Calls that report convergence (pm_pcg_solve, pm_project_step,
+ *     pm_pcg_solve_batched) synchronise that stream before returning; pm_spmv and the
+ *     kernels-only calls are asynchronous.
+ *   - Handles (pm_operator, pm_state, pm_batch) are owned by the library and released by their
+ *     destroy call. One handle must not be used from two host threads at once; different
+ *     handles may be.
+ */
+#ifndef PM_GB300_H
+#define PM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* pm_stream; /* identical to cudaStream_t */
+typedef struct pm_operator pm_operator;
+typedef struct pm_state pm_state;
+typedef struct pm_batch pm_batch;
+
+/* ---- status codes ------------------------------------------------------------------------ */
+enum {
+  PM_OK = 0,
+  PM_EINVAL = 1,        /* bad size, null pointer, depth <= 0, empty basin, unknown enum     */
+  PM_ENOMEM = 2,        /* device or host allocation failed                                   */
+  PM_ECUDA = 3,         /* a CUDA runtime call failed (message in pm_last_error)              */
+  PM_NOT_CONVERGED = 4, /* iteration cap reached; x holds the last iterate, stats are filled   */
+  PM_BREAKDOWN = 5,     /* (p, Ap) <= 0 or non-finite, or IC0 pivot failure after 11 shifts    */
+  PM_TIMEOUT = 6,       /* a bounded device-side wait ran out (persistent kernels)            */
+  PM_DISCONNECTED = 7   /* the ocean has more than one connected component                    */
+};
+
+/* Lateral outer walls that are artificial slip boundaries Gamma_1 (Section 2, Eq. prim_bot_1:
+ * u.n = 0 and zero tangential stress). Outer walls not listed, and coastlines, belong to
+ * Gamma_0 (u = 0, Eq. prim_bot_0), as does the sea floor. */
+enum { PM_WALL_WEST = 1, PM_WALL_EAST = 2, PM_WALL_SOUTH = 4, PM_WALL_NORTH = 8 };
+
+/* Basin geometry (Section 2: Omega = {(x1,x2) in Gamma_s, -h(x1,x2) < x3 < 0}).
+ * Grid nodes sit at x = i dx, y = j dy, z_k = -depth[j,i] (1 - k/(nz-1)). A hex cell is ocean
+ * when its four corner columns are ocean; columns that touch no ocean cell are dropped.
+ * ocean_mask, depth: host arrays [ny][nx] (row-major, index j*nx + i); read during the call only.
+ * ocean_mask may be NULL (all ocean); depth must be > 0 on every kept column. */
+typedef struct pm_mesh_desc {
+  int32_t nx, ny, nz;        /* nodes per axis, each >= 2                                   */
+  int32_t slip_walls;        /* PM_WALL_* bits                                              */
+  double dx, dy;             /* horizontal node spacing (> 0)                               */
+  const uint8_t* ocean_mask; /* host [ny][nx], 1 = ocean column, or NULL                    */
+  const double* depth;       /* host [ny][nx], h > 0                                        */
+} pm_mesh_desc;
+
+/* Physics of Sections 2-3: Delta_nu = sum_j nu_j d^2/dx_j^2, time step dt, Coriolis parameter
+ * f = 2 omega_3 per grid column (host [ny][nx], NULL = 0). */
+typedef struct pm_physics {
+  double nu[3];
+  double dt;
+  const double* coriolis;
+} pm_physics;
+
+/* Operators stored for a basin.
+ * VEL_Uc  : 3/(2 dt) M + K_nu with component c's homogeneous Dirichlet set eliminated
+ *           symmetrically (BDF2 prediction, Eq. fofa_velo_pred_h). Dirichlet sets: c = 1:
+ *           Gamma_0 + x-normal Gamma_1; c = 2: Gamma_0 + y-normal Gamma_1; c = 3: Gamma_0 +
+ *           Gamma_s (Eqs. pred_cl_0, pred_cl_1_u, pred_tr_3).
+ * VEL1_Uc : 1/dt M + K_nu, same sets (BDF1 start step).
+ * PRESSURE: K_I, the pure-Neumann Laplacian (Eq. fofa_q_cor_h). Solves impose zero mean.
+ * MASS    : consistent P1 mass M (Eq. fofa_velo_cor_h).
+ * GRAD_c  : G_c,ij = integral of (d phi_j / dx_c) phi_i (not symmetric; pm_spmv only).      */
+typedef enum pm_which {
+  PM_OP_VEL_U1 = 0, PM_OP_VEL_U2 = 1, PM_OP_VEL_U3 = 2,
+  PM_OP_PRESSURE = 3, PM_OP_MASS = 4,
+  PM_OP_VEL1_U1 = 5, PM_OP_VEL1_U2 = 6, PM_OP_VEL1_U3 = 7,
+  PM_OP_GRAD_X = 8, PM_OP_GRAD_Y = 9, PM_OP_GRAD_Z = 10
+} pm_which;
+
+/* Preconditioners (Section 5 remark): IC0 is the paper's choice for the velocity and mass
+ * systems (multicolour order, see DESIGN); JACOBI is the diagonal ("DIAG") and the labelled
+ * fallback; NONE is plain CG. */
+enum { PM_PREC_JACOBI = 0, PM_PREC_IC0 = 1, PM_PREC_NONE = 2 };
+/* Arithmetic of the inner iteration. FP64 throughout, or FP32 (BF16) operator values with FP32
+ * vectors inside PCG, FP64 dot products / alpha / beta, and FP64 outer iterative refinement on
+ * the true residual until rtol is met. */
+enum { PM_FP64 = 0, PM_FP32_REFINE = 1, PM_BF16_REFINE = 2 };
+
+typedef struct pm_solve_opts {
+  double rtol;           /* stop when ||b - A x||_2 <= rtol ||b||_2 (recursive residual,
+                            then confirmed on the true residual)                           */
+  int32_t max_iter;      /* cap on PCG iterations (all restarts / outer steps together)     */
+  int32_t prec;          /* PM_PREC_*                                                       */
+  int32_t precision;     /* PM_FP64, PM_FP32_REFINE, PM_BF16_REFINE                         */
+  int32_t x0_is_guess;   /* 1: x holds the initial guess; 0: start from x = 0               */
+  int32_t max_restarts;  /* true-residual restarts after the recursive test passes (FP64)   */
+  double inner_rtol;     /* mixed precision: relative reduction asked of each inner solve  */
+} pm_solve_opts;
+
+typedef struct pm_solve_stats {
+  int32_t iters;              /* PCG iterations (summed over restarts / inner solves)       */
+  int32_t outer_iters;        /* refinement steps (mixed precision), restarts (FP64)        */
+  int32_t status;             /* PM_* of this solve                                         */
+  int32_t reserved;
+  double rel_residual_true;   /* ||b - A x|| / ||b|| in FP64 at exit                         */
+  double rel_residual_rec;    /* recursive residual estimate at exit                        */
+  double seconds;             /* host wall time of the call                                 */
+  double bytes_moved;         /* algorithmic bytes (values, vectors) the iterations moved   */
+} pm_solve_stats;
+
+typedef struct pm_operator_info {
+  int64_t n;          /* nodes (rows)                                     */
+  int64_t n_pad;      /* row stride of the slot-major value arrays         */
+  int32_t ncols, nz;  /* ocean columns, nodes per column                   */
+  int32_t nx, ny;
+  int64_t device_bytes; /* device memory held by the operator now         */
+} pm_operator_info;
+
+/* ---- operator ------------------------------------------------------------------------------ */
+
+/* Build the layered mesh, boundary sets and all operators of a basin on the GPU: element
+ * integrals of Section 5 assembled row by row into a 15-slot column-sliced ELL layout.
+ * *out receives a new handle. Errors: PM_EINVAL, PM_DISCONNECTED, PM_ENOMEM, PM_ECUDA. */
+int pm_assemble_operator(const pm_mesh_desc* mesh, const pm_physics* phys, pm_operator** out,
+                         pm_stream stream);
+
+/* Device bytes pm_assemble_operator would hold for this mesh (operators, factors, workspace),
+ * for admission control by free HBM; -1 on invalid input. Host-only. */
+int64_t pm_operator_bytes(const pm_mesh_desc* mesh);
+
+int pm_operator_info_get(const pm_operator* op, pm_operator_info* info);
+
+/* Grid indices of each ocean column (host arrays of length ncols). */
+int pm_operator_columns(const pm_operator* op, int32_t* col_i, int32_t* col_j);
+
+/* Copy one operator to host for inspection: values[s * n + row] (15 slots, see DESIGN for the
+ * slot offsets), nbr[col * 7 + q] neighbour columns (-1 = none), structural slot bits per row
+ * (bit s set when row and slot neighbour share a tetrahedron). Any output may be NULL.
+ * Dirichlet elimination is applied to the VEL values as the solver sees them. Synchronous. */
+int pm_operator_export(const pm_operator* op, pm_which which, double* values, int32_t* nbr,
+                       uint16_t* structure);
+
+/* y = A x for one operator (VEL_* with its Dirichlet elimination), device vectors. Async. */
+int pm_spmv(pm_operator* op, pm_which which, const double* x, double* y, pm_stream stream);
+
+/* Solve A x = b by PCG (Section 5 remark). For PM_OP_PRESSURE the zero-mean Lagrange multiplier
+ * reading applies: b is replaced by b - (1'b / 1'm) m (m = M 1), the iterate is kept on
+ * m'x = 0, and the returned x has m'x = 0. b and x are device vectors of length n; b is not
+ * modified. stats may be NULL. Synchronises the stream. */
+int pm_pcg_solve(pm_operator* op, pm_which which, const double* b, double* x,
+                 const pm_solve_opts* opts, pm_solve_stats* stats, pm_stream stream);
+
+/* ---- projection step ---------------------------------------------------------------------- */
+
+/* Time-step state u^k, u^{k-1}, p^k (device, owned by the handle). Created at rest:
+ * u^0 = 0 (Eq. prim_ci), p^0 = 0, step index 0. */
+int pm_state_create(pm_operator* op, pm_state** out);
+/* Copy state fields to / from caller device vectors (any pointer may be NULL). Async.
+ * pm_state_set sets u^k and p^k from the given vectors (NULL = 0), sets u^{k-1} = u^k, clears
+ * the pressure-increment warm start, and sets the step index (0 = the next step is BDF1). */
+int pm_state_get(const pm_state* st, double* u1, double* u2, double* u3, double* p,
+                 pm_stream stream);
+int pm_state_set(pm_state* st, const double* u1, const double* u2, const double* u3,
+                 const double* p, int32_t step_index, pm_stream stream);
+int32_t pm_state_step_index(const pm_state* st);
+
+enum { PM_STEP_LUMPED = 0, PM_STEP_CONSISTENT = 1 };
+
+/* One BDF2 velocity-correction step (Section 3; BDF1 on the first step):
+ *   b_c = velocity right-hand side (history, advection, Coriolis, G_c^T p^k, wind tension)
+ *   (alpha M + K_nu) u~_c = b_c, c = 1..3               (velocity PCG, x0 = u^k_c)
+ *   K_I q = -alpha sum_c G_c u~_c, zero mean            (pressure PCG, x0 = previous q)
+ *   p^{k+1} = p^k + q;  u_c = u~_c + M^{-1} G_c q / alpha, then the Dirichlet sets
+ * theta1, theta2: device arrays [ncols], kinematic wind tension at the surface node of each
+ * column (NULL = 0). correction: PM_STEP_LUMPED (diag(M 1)) or PM_STEP_CONSISTENT (PCG on M
+ * with vel's options). stats: NULL or 7 entries (u1, u2, u3, q, mass1, mass2, mass3).
+ * Synchronises the stream. */
+int pm_project_step(pm_operator* op, pm_state* st, const double* theta1, const double* theta2,
+                    const pm_solve_opts* vel, const pm_solve_opts* pres, int32_t correction,
+                    pm_solve_stats* stats, pm_stream stream);
+
+void pm_operator_destroy(pm_operator* op);
+void pm_state_destroy(pm_state* st);
+
+/* ---- misc --------------------------------------------------------------------------------- */
+const char* pm_status_string(int status);
+/* Copies the calling thread's last error message (NUL-terminated) into buf; returns its length. */
+int pm_last_error(char* buf, int32_t len);
+/* Number of kernels this process has launched through the library (all threads). */
+int64_t pm_kernel_launch_count(void);
+
+/* Live kernel timing. When enabled, the PCG driver brackets every launch of the kernel classes
+ * below with CUDA events on the solve's stream and accumulates their elapsed times at its own
+ * synchronisation points. pm_kernel_timing(enable) switches it and resets the totals;
+ * pm_kernel_timing_get returns the total milliseconds and launch count of one class. Process-
+ * global and not thread-safe; a measurement aid, off by default. */
+enum { PM_KT_SPMV = 0,    /* SpMV + (p, Ap) reduction, one launch per PCG iteration      */
+       PM_KT_UPDATE = 1,  /* x, r update + residual reductions                           */
+       PM_KT_PUPDATE = 2, /* search-direction update (with the (r, z) reduction for IC0) */
+       PM_KT_IC0 = 3,     /* the 16 IC0 colour sweeps of one preconditioner apply        */
+       PM_KT_COUNT = 4 };
+int pm_kernel_timing(int32_t enable);
+int pm_kernel_timing_get(int32_t kind, double* total_ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PM_GB300_H */

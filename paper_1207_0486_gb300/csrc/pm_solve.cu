@@ -1,0 +1,800 @@
+// SpMV, preconditioner apply and preconditioned conjugate gradient on the column-sliced ELL
+// layout (Section 5 remark: the linear systems are solved by PCG; IC0 for the velocity and mass
+// systems, DIAG (Jacobi) for the pressure system with a zero-mean Lagrange multiplier).
+//
+// PCG follows Saad's preconditioned CG step for step (same order of updates, same stopping test
+// ||r|| <= rtol ||b|| on the recursive residual, then a true-residual check with restarts):
+//   K1 k_cg_spmv   : w = A p and the grid reduction (p, w); the last block forms alpha
+//   K2 k_cg_update : x += alpha p, r -= alpha w, z = D^{-1} r (Jacobi, never stored), the grid
+//                    reductions (r, r), (r, z) [and m'z, 1'r for the pressure]; the last block
+//                    tests convergence and forms beta
+//   K3 k_cg_pupd   : p = z + beta p
+// IC0 replaces the inline z by 8 forward and 8 backward colour sweeps plus a (r, z) reduction.
+// Grid reductions are deterministic: each block reduces its rows in a fixed tree, writes one
+// partial, and the last block to arrive (atomic ticket) sums the partials in block order.
+// All scalars (alpha, beta, rho, status) stay on the device; the host reads one small struct
+// every few dozen iterations to see whether the solve has finished. Kernels of iterations
+// issued after convergence return at once (the device "done" flag), so the result is the same
+// as testing after every iteration.
+#include <cmath>
+#include <cstring>
+#include <chrono>
+
+#include "pm_internal.cuh"
+
+namespace pm {
+
+struct SolveCtx {
+  int64_t n = 0;
+  double *r = nullptr, *p = nullptr, *w = nullptr, *z = nullptr, *bw = nullptr;
+  double* partials = nullptr;
+  PcgScalars* sc = nullptr;
+  PcgScalars* sc_host = nullptr;
+};
+
+struct ColourMap;  // pm_assemble.cu
+}  // namespace pm
+
+namespace pm {
+
+// ---- live kernel timing (CUDA events on the launching stream) ------------------------------------
+// When enabled, the PCG driver brackets each launch of the timed kernel classes with a pair of
+// events on the solve's stream; elapsed times are collected at the driver's own synchronisation
+// points. Process-global, not thread-safe: enable it from one host thread only.
+struct KernelTimer {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  struct Pending { cudaEvent_t a, b; int kind; int launches; };
+  std::vector<Pending> pending;
+  double total_ms[PM_KT_COUNT] = {};
+  int64_t launches[PM_KT_COUNT] = {};
+};
+static KernelTimer g_kt;
+
+static cudaEvent_t kt_event() {
+  if (!g_kt.pool.empty()) {
+    cudaEvent_t e = g_kt.pool.back();
+    g_kt.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct KtScope {
+  cudaEvent_t a = nullptr;
+  cudaStream_t s;
+  int kind, launches;
+  KtScope(int kind_, int launches_, cudaStream_t s_) : s(s_), kind(kind_), launches(launches_) {
+    if (g_kt.on) {
+      a = kt_event();
+      cudaEventRecord(a, s);
+    }
+  }
+  ~KtScope() {
+    if (a) {
+      cudaEvent_t b = kt_event();
+      cudaEventRecord(b, s);
+      g_kt.pending.push_back({a, b, kind, launches});
+    }
+  }
+};
+
+static void kt_collect() {
+  for (auto& p : g_kt.pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      g_kt.total_ms[p.kind] += ms;
+      g_kt.launches[p.kind] += p.launches;
+    }
+    g_kt.pool.push_back(p.a);
+    g_kt.pool.push_back(p.b);
+  }
+  g_kt.pending.clear();
+}
+
+namespace {
+
+constexpr int TPB = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Reduce NV per-thread values over the block; thread 0 receives the sums. sm: NV * 32 doubles.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sm) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    v[i] = warp_sum(v[i]);
+    if (lane == 0) sm[i * 32 + wid] = v[i];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double t = lane < nw ? sm[i * 32 + lane] : 0.0;
+      v[i] = warp_sum(t);
+    }
+  }
+  __syncthreads();
+}
+
+// Grid reduction with a last-block finish. Returns true in the last block; there, thread 0 holds
+// the grid totals in v. partials: NV * gridDim.x doubles; ticket: a zero-initialised counter
+// that the last block resets.
+template <int NV>
+__device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partials, uint32_t* ticket) {
+  __shared__ double sm[NV * 32];
+  __shared__ bool last;
+  block_sum<NV>(v, sm);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) partials[i * gridDim.x + blockIdx.x] = v[i];
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  double acc[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double a = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) a += __ldcg(partials + i * gridDim.x + b);
+    acc[i] = a;
+  }
+  block_sum<NV>(acc, sm);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = acc[i];
+    *ticket = 0;
+  }
+  return true;
+}
+
+__device__ __forceinline__ bool sc_done(const PcgScalars* sc) {
+  return *((volatile const int32_t*)&sc->done) != 0;
+}
+
+// Row r of the (optionally masked) operator times x. MASKC >= 0: symmetric elimination of
+// component MASKC's Dirichlet set (identity row, zero column).
+template <int MASKC, typename TV, typename TX>
+__device__ __forceinline__ double row_dot(const Geom& g, const TV* __restrict__ val, const TX* __restrict__ x,
+                                          int64_t row, int col, int k, bool& is_dir) {
+  const int nz = g.nz;
+  if (MASKC >= 0) {
+    is_dir = is_dirichlet(g.colflag[col], k, nz, MASKC);
+    if (is_dir) return (double)x[row];
+  }
+  int nb[NNBR];
+  uint8_t fl[NNBR];
+#pragma unroll
+  for (int q = 0; q < NNBR; ++q) {
+    nb[q] = q == 0 ? col : __ldg(g.nbr + (int64_t)col * NNBR + q);
+    if (MASKC >= 0) fl[q] = nb[q] >= 0 ? __ldg(g.colflag + nb[q]) : 0;
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int s = 0; s < NSLOT; ++s) {
+    const int q = slot_q(s);
+    const int kk = k + slot_dk(s);
+    if (nb[q] < 0 || kk < 0 || kk >= nz) continue;
+    if (MASKC >= 0 && is_dirichlet(fl[q], kk, nz, MASKC)) continue;
+    const double a = (double)val[(int64_t)s * g.npad + row];
+    sum = fma(a, (double)x[(int64_t)nb[q] * nz + kk], sum);
+  }
+  return sum;
+}
+
+template <int MASKC>
+__global__ void __launch_bounds__(TPB) k_spmv(Geom g, const double* __restrict__ val,
+                                              const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < g.n;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    const int col = (int)(row / g.nz);
+    const int k = (int)(row - (int64_t)col * g.nz);
+    bool d = false;
+    y[row] = row_dot<MASKC>(g, val, x, row, col, k, d);
+  }
+}
+
+// ---- PCG setup ---------------------------------------------------------------------------------
+
+// Pressure only: lam = 1'b / 1'm, xshift = m'x / 1'm.
+__global__ void __launch_bounds__(TPB) k_cg_press_sums(int64_t n, const double* __restrict__ b,
+                                                       const double* __restrict__ x, const double* __restrict__ m,
+                                                       int use_x, double* partials, PcgScalars* sc) {
+  double v[2] = {0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    v[0] += b[i];
+    if (use_x) v[1] = fma(m[i], x[i], v[1]);
+  }
+  if (grid_sum<2>(v, partials, &sc->count[0]) && threadIdx.x == 0) {
+    sc->lam = v[0] / sc->one_m;
+    sc->xshift = use_x ? v[1] / sc->one_m : 0.0;
+  }
+}
+
+// bw = b - lam m (pressure) and x = x - xshift (pressure) or x = 0 (no guess).
+__global__ void k_cg_prepare(int64_t n, const double* __restrict__ b, const double* __restrict__ m,
+                             double* __restrict__ bw, double* __restrict__ x, int press, int use_x,
+                             const PcgScalars* sc) {
+  const double lam = press ? sc->lam : 0.0, xs = press ? sc->xshift : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (press) bw[i] = b[i] - lam * m[i];
+    x[i] = use_x ? x[i] - xs : 0.0;
+  }
+}
+
+// r = bw - A x; grid sums (bw, bw) and (r, r). MODE 0: first setup (also sets tol2, zero_rhs and
+// the initial convergence test); MODE 1: true residual at exit (stores (r, r) in aux[0]).
+template <int MASKC, int MODE>
+__global__ void __launch_bounds__(TPB) k_cg_residual(Geom g, const double* __restrict__ val,
+                                                     const double* __restrict__ bw, const double* __restrict__ x,
+                                                     double* __restrict__ r, double rtol, double* partials,
+                                                     PcgScalars* sc) {
+  double v[2] = {0.0, 0.0};
+  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < g.n;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    const int col = (int)(row / g.nz);
+    const int k = (int)(row - (int64_t)col * g.nz);
+    bool d = false;
+    const double ax = row_dot<MASKC>(g, val, x, row, col, k, d);
+    const double bi = bw[row];
+    const double ri = bi - ax;
+    r[row] = ri;
+    v[0] = fma(bi, bi, v[0]);
+    v[1] = fma(ri, ri, v[1]);
+  }
+  if (grid_sum<2>(v, partials, &sc->count[1]) && threadIdx.x == 0) {
+    if (MODE == 0) {
+      sc->bb = v[0];
+      sc->rr = v[1];
+      sc->tol2 = rtol * rtol * v[0];
+      sc->zero_rhs = v[0] == 0.0;
+      sc->iter = 0;
+      sc->status = PM_OK;
+      sc->done = (v[0] == 0.0 || v[1] <= sc->tol2) ? 1 : 0;
+    } else {
+      sc->aux[0] = v[1];
+    }
+  }
+}
+
+// First preconditioned residual (Jacobi or stored z): rho = (r, z') with z' = z - c 1,
+// c = m'z / 1'm for the pressure (PROJ), p = z'. STORED: z read from zbuf.
+template <int PROJ, int STORED>
+__global__ void __launch_bounds__(TPB) k_cg_rho(int64_t n, const double* __restrict__ r, const double* __restrict__ dinv,
+                                                const double* __restrict__ zbuf, const double* __restrict__ m,
+                                                double* partials, PcgScalars* sc, int is_first) {
+  if (!is_first && sc_done(sc)) return;
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double ri = r[i];
+    const double zi = STORED ? zbuf[i] : dinv[i] * ri;
+    v[0] = fma(ri, zi, v[0]);
+    if (PROJ) {
+      v[1] = fma(m[i], zi, v[1]);
+      v[2] += ri;
+    }
+  }
+  if (grid_sum<3>(v, partials, &sc->count[2]) && threadIdx.x == 0) {
+    const double c = PROJ ? v[1] / sc->one_m : 0.0;
+    const double rho_new = v[0] - c * v[2];
+    sc->proj_c = c;
+    if (is_first) {
+      sc->rho = rho_new;
+      sc->beta = 0.0;
+    } else {
+      sc->beta = rho_new / sc->rho;
+      sc->rho = rho_new;
+    }
+    if (!(rho_new > 0.0) || !isfinite(rho_new)) {
+      if (!sc->done) {
+        sc->status = PM_BREAKDOWN;
+        sc->done = 1;
+      }
+    }
+  }
+}
+
+// p = (z - c) + beta p; beta = 0 on the first step. STORED: z from zbuf, else dinv r.
+template <int STORED>
+__global__ void __launch_bounds__(TPB) k_cg_pupd(int64_t n, const double* __restrict__ r, const double* __restrict__ dinv,
+                                                 const double* __restrict__ zbuf, double* __restrict__ p,
+                                                 const PcgScalars* sc, int is_first) {
+  if (!is_first && sc_done(sc)) return;
+  const double beta = sc->beta, c = sc->proj_c;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double zi = (STORED ? zbuf[i] : dinv[i] * r[i]) - c;
+    p[i] = is_first ? zi : fma(beta, p[i], zi);
+  }
+}
+
+// ---- PCG iteration -----------------------------------------------------------------------------
+
+template <int MASKC>
+__global__ void __launch_bounds__(TPB) k_cg_spmv(Geom g, const double* __restrict__ val, const double* __restrict__ p,
+                                                 double* __restrict__ w, double* partials, PcgScalars* sc) {
+  if (sc_done(sc)) return;
+  double v[1] = {0.0};
+  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < g.n;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    const int col = (int)(row / g.nz);
+    const int k = (int)(row - (int64_t)col * g.nz);
+    bool d = false;
+    const double wi = row_dot<MASKC>(g, val, p, row, col, k, d);
+    w[row] = wi;
+    v[0] = fma(p[row], wi, v[0]);
+  }
+  if (grid_sum<1>(v, partials, &sc->count[3]) && threadIdx.x == 0) {
+    const double pap = v[0];
+    sc->pAp = pap;
+    if (!(pap > 0.0) || !isfinite(pap)) {
+      sc->status = PM_BREAKDOWN;
+      sc->done = 1;
+    } else {
+      sc->alpha = sc->rho / pap;
+    }
+  }
+}
+
+// x += alpha p; r -= alpha w; (Jacobi, INLINE_Z) z = dinv r and its dots, else only (r, r).
+template <int PROJ, int INLINE_Z>
+__global__ void __launch_bounds__(TPB) k_cg_update(int64_t n, double* __restrict__ x, double* __restrict__ r,
+                                                   const double* __restrict__ p, const double* __restrict__ w,
+                                                   const double* __restrict__ dinv, const double* __restrict__ m,
+                                                   double* partials, PcgScalars* sc) {
+  if (sc_done(sc)) return;
+  const double alpha = sc->alpha;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const double ri = fma(-alpha, w[i], r[i]);
+    r[i] = ri;
+    v[0] = fma(ri, ri, v[0]);
+    if (INLINE_Z) {
+      const double zi = dinv[i] * ri;
+      v[1] = fma(ri, zi, v[1]);
+      if (PROJ) {
+        v[2] = fma(m[i], zi, v[2]);
+        v[3] += ri;
+      }
+    }
+  }
+  if (grid_sum<4>(v, partials, &sc->count[4]) && threadIdx.x == 0) {
+    sc->iter += 1;
+    sc->rr = v[0];
+    if (v[0] <= sc->tol2) {
+      sc->done = 1;
+    } else if (sc->iter >= sc->max_iter) {
+      sc->status = PM_NOT_CONVERGED;
+      sc->done = 1;
+    } else if (INLINE_Z) {
+      const double c = PROJ ? v[2] / sc->one_m : 0.0;
+      const double rho_new = v[1] - c * v[3];
+      sc->proj_c = c;
+      sc->beta = rho_new / sc->rho;
+      sc->rho = rho_new;
+      if (!(rho_new > 0.0) || !isfinite(rho_new)) {
+        sc->status = PM_BREAKDOWN;
+        sc->done = 1;
+      }
+    }
+  }
+}
+
+// ---- IC0 colour sweeps -------------------------------------------------------------------------
+struct CMap {
+  int64_t cbase[8];
+  int32_t nlev[2];
+};
+
+// Forward (FWD = 1): y_i = (r_i - sum_{colour(j) < c} L_ij y_j) / L_ii over rows of colour c.
+// Backward (FWD = 0): z_i = (y_i - sum_{colour(j) > c} L_ji z_j) / L_ii, in place on y.
+template <int COLOUR, int FWD>
+__global__ void __launch_bounds__(TPB) k_ic0_sweep(Geom g, CMap cm, const int32_t* __restrict__ cls_cols,
+                                                   int64_t cls_off, int64_t cls_cnt, const double* __restrict__ F,
+                                                   const double* __restrict__ r, double* __restrict__ y,
+                                                   const PcgScalars* sc, int check_done) {
+  if (check_done && sc_done(sc)) return;
+  constexpr int kpar = COLOUR >> 2;
+  const int nlev = cm.nlev[kpar];
+  const int64_t total = cls_cnt * nlev;
+  const int nz = g.nz;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int col = __ldg(cls_cols + cls_off + t / nlev);
+    const int k = 2 * (int)(t % nlev) + kpar;
+    const int64_t row = (int64_t)col * nz + k;
+    const int64_t pi = cm.cbase[COLOUR] + t;
+    double acc = FWD ? r[row] : y[row];
+#pragma unroll
+    for (int s = 0; s < NSLOT; ++s) {
+      if (s == DIAG_SLOT) continue;
+      constexpr int dummy = 0;
+      (void)dummy;
+      const int cj = COLOUR ^ slot_flip(s);
+      if (FWD ? (cj > COLOUR) : (cj < COLOUR)) continue;
+      const int q = slot_q(s);
+      const int kk = k + slot_dk(s);
+      if (kk < 0 || kk >= nz) continue;
+      const int nb = q == 0 ? col : __ldg(g.nbr + (int64_t)col * NNBR + q);
+      if (nb < 0) continue;
+      acc = fma(-F[(int64_t)s * g.n + pi], y[(int64_t)nb * nz + kk], acc);
+    }
+    y[row] = acc / F[(int64_t)DIAG_SLOT * g.n + pi];
+  }
+}
+
+// Grid of the reduction kernels: at most MAX_GRID blocks (the size of the partials buffer).
+int grid_for(int64_t n, int threads, int sms) {
+  int64_t gsz = (n + threads - 1) / threads;
+  int64_t cap = (int64_t)sms * 8;
+  if (cap > MAX_GRID) cap = MAX_GRID;
+  if (gsz > cap) gsz = cap;
+  if (gsz < 1) gsz = 1;
+  return (int)gsz;
+}
+
+CMap cmap_of(const pm_operator* op) {
+  CMap cm;
+  cm.nlev[0] = (op->nz + 1) / 2;
+  cm.nlev[1] = op->nz / 2;
+  int64_t acc = 0;
+  for (int c = 0; c < 8; ++c) {
+    cm.cbase[c] = acc;
+    acc += (int64_t)op->cls_count[c & 3] * cm.nlev[c >> 2];
+  }
+  return cm;
+}
+
+void ic0_apply(pm_operator* op, int which, const double* r, double* z, const PcgScalars* sc,
+               int check_done, cudaStream_t s) {
+  Geom g = geom_of(op);
+  CMap cm = cmap_of(op);
+  const double* F = op->ic0[which].F;
+  int64_t off[5] = {0, 0, 0, 0, 0};
+  for (int c = 0; c < 4; ++c) off[c + 1] = off[c] + op->cls_count[c];
+#define PM_SWEEP(C, FW)                                                                        \
+  {                                                                                            \
+    const int64_t cnt = op->cls_count[(C) & 3];                                                \
+    const int64_t tot = cnt * cm.nlev[(C) >> 2];                                               \
+    if (tot > 0) {                                                                             \
+      k_ic0_sweep<C, FW><<<grid_for(tot, TPB, op->num_sms), TPB, 0, s>>>(                      \
+          g, cm, op->d_cls_cols, off[(C) & 3], cnt, F, r, z, sc, check_done);                  \
+      count_launch();                                                                          \
+    }                                                                                          \
+  }
+  PM_SWEEP(0, 1) PM_SWEEP(1, 1) PM_SWEEP(2, 1) PM_SWEEP(3, 1)
+  PM_SWEEP(4, 1) PM_SWEEP(5, 1) PM_SWEEP(6, 1) PM_SWEEP(7, 1)
+  PM_SWEEP(7, 0) PM_SWEEP(6, 0) PM_SWEEP(5, 0) PM_SWEEP(4, 0)
+  PM_SWEEP(3, 0) PM_SWEEP(2, 0) PM_SWEEP(1, 0) PM_SWEEP(0, 0)
+#undef PM_SWEEP
+}
+
+int ensure_ctx(pm_operator* op) {
+  if (op->ctx) return PM_OK;
+  SolveCtx* c = new SolveCtx();
+  c->n = op->n;
+  const size_t vb = (size_t)op->n * sizeof(double);
+  cudaError_t e = cudaSuccess;
+  e = e ? e : cudaMalloc((void**)&c->r, vb);
+  e = e ? e : cudaMalloc((void**)&c->p, vb);
+  e = e ? e : cudaMalloc((void**)&c->w, vb);
+  e = e ? e : cudaMalloc((void**)&c->z, vb);
+  e = e ? e : cudaMalloc((void**)&c->bw, vb);
+  e = e ? e : cudaMalloc((void**)&c->partials, (size_t)NPART * MAX_GRID * sizeof(double));
+  e = e ? e : cudaMalloc((void**)&c->sc, sizeof(PcgScalars));
+  e = e ? e : cudaMallocHost((void**)&c->sc_host, sizeof(PcgScalars));
+  if (e == cudaSuccess) e = cudaMemset(c->sc, 0, sizeof(PcgScalars));
+  op->ctx = c;
+  if (e != cudaSuccess) return cuda_check(e, "solve workspace");
+  op->device_bytes += 5 * (int64_t)vb + (int64_t)NPART * MAX_GRID * 8 + (int64_t)sizeof(PcgScalars);
+  return PM_OK;
+}
+
+template <int MASKC>
+void launch_iter(pm_operator* op, int which, const double* val, double* x, bool proj, bool ic0,
+                 const double* dinv, cudaStream_t s) {
+  SolveCtx* c = op->ctx;
+  Geom g = geom_of(op);
+  const int G = grid_for(op->n, TPB, op->num_sms);
+  {
+    KtScope t(PM_KT_SPMV, 1, s);
+    k_cg_spmv<MASKC><<<G, TPB, 0, s>>>(g, val, c->p, c->w, c->partials, c->sc);
+  }
+  if (!ic0) {
+    {
+      KtScope t(PM_KT_UPDATE, 1, s);
+      if (proj) {
+        k_cg_update<1, 1><<<G, TPB, 0, s>>>(op->n, x, c->r, c->p, c->w, dinv, op->d_m, c->partials, c->sc);
+      } else {
+        k_cg_update<0, 1><<<G, TPB, 0, s>>>(op->n, x, c->r, c->p, c->w, dinv, op->d_m, c->partials, c->sc);
+      }
+    }
+    {
+      KtScope t(PM_KT_PUPDATE, 1, s);
+      k_cg_pupd<0><<<G, TPB, 0, s>>>(op->n, c->r, dinv, nullptr, c->p, c->sc, 0);
+    }
+    count_launch(3);
+  } else {
+    {
+      KtScope t(PM_KT_UPDATE, 1, s);
+      k_cg_update<0, 0><<<G, TPB, 0, s>>>(op->n, x, c->r, c->p, c->w, dinv, op->d_m, c->partials, c->sc);
+    }
+    count_launch(1);
+    {
+      KtScope t(PM_KT_IC0, 16, s);
+      ic0_apply(op, which, c->r, c->z, c->sc, 1, s);
+    }
+    {
+      KtScope t(PM_KT_PUPDATE, 2, s);
+      if (proj) {
+        k_cg_rho<1, 1><<<G, TPB, 0, s>>>(op->n, c->r, dinv, c->z, op->d_m, c->partials, c->sc, 0);
+      } else {
+        k_cg_rho<0, 1><<<G, TPB, 0, s>>>(op->n, c->r, dinv, c->z, op->d_m, c->partials, c->sc, 0);
+      }
+      k_cg_pupd<1><<<G, TPB, 0, s>>>(op->n, c->r, dinv, c->z, c->p, c->sc, 0);
+    }
+    count_launch(2);
+  }
+}
+
+template <int MASKC>
+void launch_residual(pm_operator* op, const double* val, const double* bw, const double* x, double rtol,
+                     int mode, cudaStream_t s) {
+  SolveCtx* c = op->ctx;
+  Geom g = geom_of(op);
+  const int G = grid_for(op->n, TPB, op->num_sms);
+  if (mode == 0)
+    k_cg_residual<MASKC, 0><<<G, TPB, 0, s>>>(g, val, bw, x, c->r, rtol, c->partials, c->sc);
+  else
+    k_cg_residual<MASKC, 1><<<G, TPB, 0, s>>>(g, val, bw, x, c->r, rtol, c->partials, c->sc);
+  count_launch();
+}
+
+// z, p, rho from the current r (first step or restart). The kernels run even when "done" is
+// set by the setup so that a zero initial residual still leaves consistent scalars.
+void launch_first(pm_operator* op, int which, bool proj, bool ic0, const double* dinv, cudaStream_t s) {
+  SolveCtx* c = op->ctx;
+  const int G = grid_for(op->n, TPB, op->num_sms);
+  if (ic0) {
+    ic0_apply(op, which, c->r, c->z, c->sc, 0, s);
+    if (proj) k_cg_rho<1, 1><<<G, TPB, 0, s>>>(op->n, c->r, dinv, c->z, op->d_m, c->partials, c->sc, 1);
+    else k_cg_rho<0, 1><<<G, TPB, 0, s>>>(op->n, c->r, dinv, c->z, op->d_m, c->partials, c->sc, 1);
+    k_cg_pupd<1><<<G, TPB, 0, s>>>(op->n, c->r, dinv, c->z, c->p, c->sc, 1);
+  } else {
+    if (proj) k_cg_rho<1, 0><<<G, TPB, 0, s>>>(op->n, c->r, dinv, nullptr, op->d_m, c->partials, c->sc, 1);
+    else k_cg_rho<0, 0><<<G, TPB, 0, s>>>(op->n, c->r, dinv, nullptr, op->d_m, c->partials, c->sc, 1);
+    k_cg_pupd<0><<<G, TPB, 0, s>>>(op->n, c->r, dinv, nullptr, c->p, c->sc, 1);
+  }
+  count_launch(2);
+}
+
+__global__ void k_fill(double* x, int64_t n, double v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) x[i] = v;
+}
+__global__ void k_shift_by(double* x, int64_t n, const PcgScalars* sc) {
+  const double v = sc->xshift;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) x[i] -= v;
+}
+
+int read_scalars(SolveCtx* c, cudaStream_t s) {
+  int st = cuda_check(cudaMemcpyAsync(c->sc_host, c->sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s), "scalars");
+  if (st) return st;
+  st = cuda_check(cudaStreamSynchronize(s), "pcg sync");
+  if (!st && !g_kt.pending.empty()) kt_collect();
+  return st;
+}
+
+// Algorithmic bytes of one PCG iteration per row (FP64): SpMV 15 values + p read + w write,
+// update x, r read/write + p, w, dinv read, p-update r, dinv, p read + p write.
+double bytes_per_iter(const pm_operator* op, bool ic0) {
+  const double n = (double)op->n;
+  double b = n * (15 * 8 + 8 + 8) + n * (5 * 8 + 2 * 8) + n * (3 * 8 + 8);
+  if (ic0) b += n * (2 * 8 * 8 + 4 * 8);
+  return b;
+}
+
+template <int MASKC>
+int pcg_run(pm_operator* op, int which, const double* b, double* x, const pm_solve_opts* o,
+            pm_solve_stats* stats, cudaStream_t s) {
+  auto t0 = std::chrono::steady_clock::now();
+  SolveCtx* c = op->ctx;
+  const bool proj = which == PM_OP_PRESSURE;
+  const bool ic0 = o->prec == PM_PREC_IC0;
+  const double* val = op->d_val[which_valset(which)];
+  int st;
+  // Preconditioner set-up.
+  const double* dinv = nullptr;
+  if ((st = launch_dinv(op, which, s))) return st;
+  dinv = op->d_dinv[which];
+  double* ones_buf = nullptr;
+  if (o->prec == PM_PREC_NONE) {
+    ones_buf = c->z;  // plain CG: z = r, held as dinv = 1 in a scratch vector
+    k_fill<<<grid_for(op->n, TPB, op->num_sms), TPB, 0, s>>>(ones_buf, op->n, 1.0);
+    count_launch();
+    dinv = ones_buf;
+  }
+  if (ic0) {
+    Ic0Factor& f = op->ic0[which];
+    if (!f.ok) {
+      int bd = 0;
+      double shift = 0.0;
+      for (int m = -1; m <= 10; ++m) {
+        shift = m < 0 ? 0.0 : 1e-3 * std::pow(2.0, m);
+        if ((st = launch_ic0_factor(op, which, shift, &bd, s))) return st;
+        if (!bd) break;
+      }
+      if (bd) return set_error(PM_BREAKDOWN, "IC0 pivot failure after the shift limit");
+    }
+  }
+  // Right-hand side and initial guess.
+  const int G = grid_for(op->n, TPB, op->num_sms);
+  PcgScalars init;
+  std::memset(&init, 0, sizeof(init));
+  init.one_m = op->one_m;
+  init.max_iter = o->max_iter;
+  if ((st = cuda_check(cudaMemcpyAsync(c->sc, &init, sizeof(init), cudaMemcpyHostToDevice, s), "scalars init"))) return st;
+  const double* bw = b;
+  if (proj) {
+    k_cg_press_sums<<<G, TPB, 0, s>>>(op->n, b, x, op->d_m, o->x0_is_guess ? 1 : 0, c->partials, c->sc);
+    k_cg_prepare<<<G, TPB, 0, s>>>(op->n, b, op->d_m, c->bw, x, 1, o->x0_is_guess ? 1 : 0, c->sc);
+    count_launch(2);
+    bw = c->bw;
+  } else if (!o->x0_is_guess) {
+    k_cg_prepare<<<G, TPB, 0, s>>>(op->n, b, op->d_m, nullptr, x, 0, 0, c->sc);
+    count_launch();
+  }
+  launch_residual<MASKC>(op, val, bw, x, o->rtol, 0, s);
+  launch_first(op, which, proj, ic0, dinv, s);
+  if ((st = read_scalars(c, s))) return st;
+  int restarts = 0;
+  int status = PM_OK;
+  double rel_true = 0.0;
+  if (c->sc_host->zero_rhs) {
+    k_fill<<<G, TPB, 0, s>>>(x, op->n, 0.0);
+    count_launch();
+    if ((st = read_scalars(c, s))) return st;
+  } else {
+    int64_t issued = 0;
+    for (;;) {
+      int chunk = 4;
+      while (!c->sc_host->done) {
+        // the device stops itself at max_iter; this bound only guards the host loop
+        if (issued > (int64_t)o->max_iter + 4096)
+          return set_error(PM_ECUDA, "PCG driver: device never reported completion");
+        for (int it = 0; it < chunk; ++it) launch_iter<MASKC>(op, which, val, x, proj, ic0, dinv, s);
+        issued += chunk;
+        if ((st = read_scalars(c, s))) return st;
+        if (chunk < 64) chunk *= 2;
+      }
+      status = c->sc_host->status;
+      // true residual
+      launch_residual<MASKC>(op, val, bw, x, o->rtol, 1, s);
+      if ((st = read_scalars(c, s))) return st;
+      rel_true = std::sqrt(c->sc_host->aux[0] / c->sc_host->bb);
+      if (status != PM_OK || rel_true <= o->rtol || restarts >= o->max_restarts ||
+          c->sc_host->iter >= o->max_iter)
+        break;
+      ++restarts;
+      // restart from the true residual held in r
+      PcgScalars* hs = c->sc_host;
+      hs->done = 0;
+      hs->rr = hs->aux[0];
+      if ((st = cuda_check(cudaMemcpyAsync(c->sc, hs, sizeof(PcgScalars), cudaMemcpyHostToDevice, s), "scalars"))) return st;
+      launch_first(op, which, proj, ic0, dinv, s);
+      if ((st = read_scalars(c, s))) return st;
+    }
+    if (status == PM_OK && rel_true > o->rtol) status = PM_NOT_CONVERGED;
+  }
+  if (proj) {
+    // keep m'x = 0 exactly as returned result
+    k_cg_press_sums<<<G, TPB, 0, s>>>(op->n, b, x, op->d_m, 1, c->partials, c->sc);
+    k_shift_by<<<G, TPB, 0, s>>>(x, op->n, c->sc);
+    count_launch(2);
+    if ((st = read_scalars(c, s))) return st;
+  }
+  const PcgScalars* h = c->sc_host;
+  if (stats) {
+    stats->iters = h->iter;
+    stats->outer_iters = restarts;
+    stats->status = status;
+    stats->rel_residual_true = h->zero_rhs ? 0.0 : rel_true;
+    stats->rel_residual_rec = h->zero_rhs ? 0.0 : std::sqrt(h->rr / h->bb);
+    stats->bytes_moved = h->iter * bytes_per_iter(op, ic0);
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if ((st = cuda_check(cudaGetLastError(), "pcg kernels"))) return st;
+  if (status != PM_OK) {
+    return set_error(status, status == PM_NOT_CONVERGED ? "PCG did not reach rtol within max_iter"
+                                                        : "PCG breakdown: (p, Ap) <= 0 or non-finite");
+  }
+  return PM_OK;
+}
+
+}  // namespace
+
+int spmv(pm_operator* op, int which, const double* x, double* y, cudaStream_t s) {
+  const int vs = which_valset(which);
+  if (vs < 0) return set_error(PM_EINVAL, "unknown operator");
+  Geom g = geom_of(op);
+  const int G = grid_for(op->n, TPB, op->num_sms);
+  switch (which_mask(which)) {
+    case 0: k_spmv<0><<<G, TPB, 0, s>>>(g, op->d_val[vs], x, y); break;
+    case 1: k_spmv<1><<<G, TPB, 0, s>>>(g, op->d_val[vs], x, y); break;
+    case 2: k_spmv<2><<<G, TPB, 0, s>>>(g, op->d_val[vs], x, y); break;
+    default: k_spmv<-1><<<G, TPB, 0, s>>>(g, op->d_val[vs], x, y); break;
+  }
+  count_launch();
+  return cuda_check(cudaGetLastError(), "k_spmv");
+}
+
+int pcg_solve(pm_operator* op, int which, const double* b, double* x, const pm_solve_opts* o,
+              pm_solve_stats* st, cudaStream_t s) {
+  if (!which_symmetric(which)) return set_error(PM_EINVAL, "pcg needs a symmetric operator");
+  if (o->prec < 0 || o->prec > PM_PREC_NONE) return set_error(PM_EINVAL, "unknown preconditioner");
+  if (!(o->rtol > 0.0) || o->max_iter < 0) return set_error(PM_EINVAL, "rtol must be > 0, max_iter >= 0");
+  int r = ensure_ctx(op);
+  if (r) return r;
+  switch (which_mask(which)) {
+    case 0: return pcg_run<0>(op, which, b, x, o, st, s);
+    case 1: return pcg_run<1>(op, which, b, x, o, st, s);
+    case 2: return pcg_run<2>(op, which, b, x, o, st, s);
+    default: return pcg_run<-1>(op, which, b, x, o, st, s);
+  }
+}
+
+}  // namespace pm
+
+extern "C" int pm_kernel_timing(int32_t enable) {
+  using namespace pm;
+  if (!g_kt.pending.empty()) {
+    cudaDeviceSynchronize();
+    kt_collect();
+  }
+  g_kt.on = enable != 0;
+  for (int k = 0; k < PM_KT_COUNT; ++k) {
+    g_kt.total_ms[k] = 0.0;
+    g_kt.launches[k] = 0;
+  }
+  return PM_OK;
+}
+
+extern "C" int pm_kernel_timing_get(int32_t kind, double* total_ms, int64_t* launches) {
+  using namespace pm;
+  if (kind < 0 || kind >= PM_KT_COUNT) return set_error(PM_EINVAL, "unknown kernel class");
+  if (!g_kt.pending.empty()) {
+    cudaDeviceSynchronize();
+    kt_collect();
+  }
+  if (total_ms) *total_ms = g_kt.total_ms[kind];
+  if (launches) *launches = g_kt.launches[kind];
+  return PM_OK;
+}
+
+namespace pm {
+
+void destroy_ctx(pm_operator* op) {
+  SolveCtx* c = op->ctx;
+  if (!c) return;
+  cudaFree(c->r);
+  cudaFree(c->p);
+  cudaFree(c->w);
+  cudaFree(c->z);
+  cudaFree(c->bw);
+  cudaFree(c->partials);
+  cudaFree(c->sc);
+  cudaFreeHost(c->sc_host);
+  delete c;
+  op->ctx = nullptr;
+}
+
+}  // namespace pm

@@ -1,0 +1,85 @@
+"""CPU checks of the C ABI library: it builds, loads and exports every symbol of include/pm.h."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pm.h")
+
+
+def header_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = re.findall(r"\b(pm_[a-z0-9_]+)\s*\(", txt)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_1207_0486_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = header_functions()
+    for required in ("pm_assemble_operator", "pm_pcg_solve", "pm_project_step"):
+        assert required in names
+
+
+def test_library_exports_every_header_symbol(lib_path):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(pm_[a-z0-9_]+)", out))
+    missing = [n for n in header_functions() if n not in exported]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header(lib_path):
+    import paper_1207_0486_gb300.api as api
+    lib = api.load()
+    assert set(header_functions()) == set(api.SIGNATURES), set(header_functions()) ^ set(api.SIGNATURES)
+    assert lib.pm_kernel_launch_count() == 0
+    assert lib.pm_status_string(api.PM_BREAKDOWN) == b"breakdown"
+
+
+def test_host_side_validation_without_gpu(lib_path):
+    """Argument checks run on the host and return PM_EINVAL without touching a GPU."""
+    import ctypes
+
+    import numpy as np
+
+    import paper_1207_0486_gb300.api as api
+    lib = api.load()
+    h = ctypes.c_void_p()
+    depth = np.ones((4, 4))
+    d = api.MeshDesc(1, 4, 4, 0, 1.0, 1.0, None, depth.ctypes.data)
+    ph = api.Physics((ctypes.c_double * 3)(1, 1, 1), 1.0, None)
+    assert lib.pm_assemble_operator(ctypes.byref(d), ctypes.byref(ph), ctypes.byref(h), None) == api.PM_EINVAL
+    buf = ctypes.create_string_buffer(256)
+    lib.pm_last_error(buf, 256)
+    assert b">= 2" in buf.value
+    # two separate ocean patches -> PM_DISCONNECTED
+    mask = np.zeros((6, 9), dtype=np.uint8)
+    mask[:, 0:3] = 1
+    mask[:, 6:9] = 1
+    depth = np.ones((6, 9))
+    d = api.MeshDesc(9, 6, 3, 0, 1.0, 1.0, mask.ctypes.data, depth.ctypes.data)
+    assert lib.pm_assemble_operator(ctypes.byref(d), ctypes.byref(ph), ctypes.byref(h), None) == api.PM_DISCONNECTED
+    # non-positive depth on an ocean column
+    mask = np.ones((4, 4), dtype=np.uint8)
+    depth = np.ones((4, 4))
+    depth[2, 2] = 0.0
+    d = api.MeshDesc(4, 4, 3, 0, 1.0, 1.0, mask.ctypes.data, depth.ctypes.data)
+    assert lib.pm_assemble_operator(ctypes.byref(d), ctypes.byref(ph), ctypes.byref(h), None) == api.PM_EINVAL
+    ph_bad = api.Physics((ctypes.c_double * 3)(1, 1, 1), 0.0, None)
+    depth[2, 2] = 1.0
+    assert lib.pm_assemble_operator(ctypes.byref(d), ctypes.byref(ph_bad), ctypes.byref(h), None) == api.PM_EINVAL
+
+
+def test_operator_bytes_scales(lib_path):
+    import paper_1207_0486_gb300.api as api
+    from workloads import box_basin
+    b1 = api.operator_bytes(box_basin(nh=16, nz=8))
+    b2 = api.operator_bytes(box_basin(nh=32, nz=8))
+    assert b1 > 0 and 3.5 < b2 / b1 < 4.5

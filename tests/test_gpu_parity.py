@@ -1,0 +1,220 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle, element by element."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from gpu_util import ell_to_csr, rel_rowwise, theta_basin  # noqa: E402
+from oracle import fem, mesh as omesh, pcg as opcg, step as ostep  # noqa: E402
+from test_oracle_fem import small_basin  # noqa: E402
+from workloads import box_basin, ocean_basin, random_vector  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+import paper_1207_0486_gb300 as pm  # noqa: E402
+
+WHICH_ALL = [pm.OP_VEL_U1, pm.OP_VEL_U2, pm.OP_VEL_U3, pm.OP_VEL1_U1, pm.OP_VEL1_U2, pm.OP_VEL1_U3,
+             pm.OP_PRESSURE, pm.OP_MASS, pm.OP_GRAD_X, pm.OP_GRAD_Y, pm.OP_GRAD_Z]
+
+
+def basin_cases():
+    return {
+        "box16": lambda: theta_basin(box_basin()),
+        "small": lambda: small_basin(),
+        "ocean48": lambda: ocean_basin(nx=48, ny=40, nz=9, dx=1e5),
+        "box2": lambda: box_basin(nh=2, nz=2),
+    }
+
+
+_cache = {}
+
+
+def case(name):
+    if name not in _cache:
+        b = basin_cases()[name]()
+        _cache[name] = (b, pm.assemble_operator(b), fem.assemble(b))
+    return _cache[name]
+
+
+def oracle_matrix(ops, which):
+    if which in (pm.OP_VEL_U1, pm.OP_VEL_U2, pm.OP_VEL_U3):
+        return ops.A_u(which - pm.OP_VEL_U1, bdf1=False)
+    if which in (pm.OP_VEL1_U1, pm.OP_VEL1_U2, pm.OP_VEL1_U3):
+        return ops.A_u(which - pm.OP_VEL1_U1, bdf1=True)
+    if which == pm.OP_PRESSURE:
+        return ops.K_I
+    if which == pm.OP_MASS:
+        return ops.M
+    return ops.G[which - pm.OP_GRAD_X]
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def mask_of(ops, which):
+    if which in (pm.OP_VEL_U1, pm.OP_VEL_U2, pm.OP_VEL_U3):
+        return ops.mesh.dirichlet[which - pm.OP_VEL_U1]
+    if which in (pm.OP_VEL1_U1, pm.OP_VEL1_U2, pm.OP_VEL1_U3):
+        return ops.mesh.dirichlet[which - pm.OP_VEL1_U1]
+    return None
+
+
+@pytest.mark.parametrize("name", ["box16", "small", "ocean48", "box2"])
+def test_node_order_and_columns(name):
+    b, op, ops = case(name)
+    assert op.n == ops.n and op.ncols == ops.mesh.ncols
+    ci, cj = op.columns()
+    assert np.array_equal(ci, ops.mesh.col_i) and np.array_equal(cj, ops.mesh.col_j)
+
+
+@pytest.mark.parametrize("name", ["box16", "small", "ocean48", "box2"])
+def test_assembly_matches_oracle(name):
+    b, op, ops = case(name)
+    for which in WHICH_ALL:
+        vals, nbr, st = op.export(which)
+        A = ell_to_csr(vals, nbr, op.nz, structure=st)
+        B = oracle_matrix(ops, which)
+        assert rel_rowwise(A, B) <= 1e-12, (name, which)
+        # structural pattern: bit-exact equality with the oracle's sparsity
+        Ap = ell_to_csr(np.ones_like(vals), nbr, op.nz, structure=st)
+        Bp = B.copy()
+        Bp.data[:] = 1.0
+        assert (Ap != Bp).nnz == 0, (name, which)
+
+
+@pytest.mark.parametrize("name", ["box16", "small", "ocean48"])
+def test_spmv_matches_oracle(name):
+    b, op, ops = case(name)
+    x = random_vector(op.n, 5)
+    xd = dev(x)
+    for which in WHICH_ALL:
+        y = torch.empty_like(xd)
+        op.spmv(which, xd, y)
+        torch.cuda.synchronize()
+        A = oracle_matrix(ops, which)
+        yo = A @ x
+        scale = abs(A) @ abs(x)
+        err = np.abs(y.cpu().numpy() - yo).max() / max(scale.max(), 1e-300)
+        assert err <= 1e-14, (name, which, err)
+
+
+def _rhs(ops, which, seed):
+    b = random_vector(ops.n, seed)
+    m = mask_of(ops, which)
+    if m is not None:
+        b[m] = 0.0
+    return b
+
+
+def _oracle_solve(ops, which, b, rtol, prec, max_iter=200000):
+    A = oracle_matrix(ops, which)
+    if prec == pm.PREC_JACOBI:
+        P = opcg.jacobi_preconditioner(A)
+    elif prec == pm.PREC_IC0:
+        P = opcg.ic0_preconditioner(A, ops.mesh.colour)[0]
+    else:
+        P = None
+    if which == pm.OP_PRESSURE:
+        return opcg.pressure_solve(A, ops.m, b, rtol=rtol, precond=P, max_iter=max_iter)
+    return opcg.pcg(A, b, rtol=rtol, precond=P, max_iter=max_iter)
+
+
+SOLVE_CASES = [(w, p) for w in (pm.OP_VEL_U1, pm.OP_VEL_U2, pm.OP_VEL_U3, pm.OP_VEL1_U1, pm.OP_MASS)
+               for p in (pm.PREC_JACOBI, pm.PREC_IC0, pm.PREC_NONE)] + \
+              [(pm.OP_PRESSURE, pm.PREC_JACOBI), (pm.OP_PRESSURE, pm.PREC_IC0)]
+
+
+@pytest.mark.parametrize("name", ["box16", "small", "ocean48"])
+@pytest.mark.parametrize("which,prec", SOLVE_CASES)
+def test_pcg_iterations_and_solution(name, which, prec):
+    b, op, ops = case(name)
+    rhs = _rhs(ops, which, 17 + which)
+    bd = dev(rhs)
+    # iteration counts at a working tolerance
+    rtol = 1e-10
+    x = torch.zeros_like(bd)
+    st = op.solve(which, bd, x, pm.Options(rtol=rtol, prec=prec))
+    ref = _oracle_solve(ops, which, rhs, rtol, prec)
+    assert st.status == pm.PM_OK
+    assert abs(st.iters - ref.iters) <= 2, (st.iters, ref.iters)
+    assert st.rel_residual_true <= rtol
+    # solution at a tight tolerance: both sides converged far below the 1e-9 parity bar
+    tight = 1e-12 if which == pm.OP_PRESSURE else 1e-13
+    x = torch.zeros_like(bd)
+    st = op.solve(which, bd, x, pm.Options(rtol=tight, prec=prec, max_restarts=5), allow_not_converged=True)
+    ref = _oracle_solve(ops, which, rhs, tight, prec)
+    xg = x.cpu().numpy()
+    err = np.linalg.norm(xg - ref.x) / np.linalg.norm(ref.x)
+    assert err <= 1e-9, err
+    if which == pm.OP_PRESSURE:
+        assert abs(ops.m @ xg) <= 1e-12 * np.abs(xg).max() * ops.m.sum()
+
+
+@pytest.mark.parametrize("which", [pm.OP_VEL_U1, pm.OP_PRESSURE])
+def test_warm_start_and_iteration_cap(which):
+    b, op, ops = case("small")
+    rhs = _rhs(ops, which, 3)
+    x0 = _rhs(ops, which, 4) * 1e-3
+    bd = dev(rhs)
+    for cap in (1, 5):
+        x = dev(x0)
+        st = op.solve(which, bd, x, pm.Options(rtol=1e-14, max_iter=cap, prec=pm.PREC_JACOBI, x0_is_guess=True,
+                                               max_restarts=0), allow_not_converged=True)
+        assert st.status == pm.PM_NOT_CONVERGED and st.iters == cap
+        A = oracle_matrix(ops, which)
+        P = opcg.jacobi_preconditioner(A)
+        if which == pm.OP_PRESSURE:
+            ref = opcg.pressure_solve(A, ops.m, rhs, x0=x0, rtol=1e-14, precond=P, max_iter=cap, max_restarts=0)
+        else:
+            ref = opcg.pcg(A, rhs, x0=x0, rtol=1e-14, precond=P, max_iter=cap, max_restarts=0)
+        err = np.abs(x.cpu().numpy() - ref.x).max() / np.abs(ref.x).max()
+        assert err <= 1e-11, (cap, err)
+
+
+def test_zero_rhs_gives_zero():
+    b, op, ops = case("small")
+    bd = torch.zeros(op.n, dtype=torch.float64, device="cuda")
+    x = torch.ones_like(bd)
+    st = op.solve(pm.OP_VEL_U1, bd, x, pm.Options(x0_is_guess=True, prec=pm.PREC_IC0))
+    assert st.iters == 0 and float(x.abs().max()) == 0.0
+
+
+def test_bad_arguments_raise():
+    b, op, ops = case("small")
+    x = torch.zeros(op.n, dtype=torch.float32, device="cuda")
+    with pytest.raises(ValueError):
+        op.solve(pm.OP_VEL_U1, x, x)
+    xd = torch.zeros(op.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(pm.PMError):
+        op.solve(pm.OP_GRAD_X, xd, xd)
+
+
+@pytest.mark.parametrize("name", ["box16", "small", "ocean48"])
+@pytest.mark.parametrize("correction", [pm.STEP_LUMPED, pm.STEP_CONSISTENT])
+def test_project_step_matches_oracle(name, correction):
+    b, op, ops = case(name)
+    if b.theta is None:
+        theta_basin(b)
+        ops = fem.assemble(b)
+    st = pm.State(op)
+    t1 = dev(op.column_field(b.theta[0]))
+    t2 = dev(op.column_field(b.theta[1]))
+    tol = 1e-12
+    vel = pm.Options(rtol=tol, prec=pm.PREC_IC0, max_restarts=5)
+    pres = pm.Options(rtol=tol, prec=pm.PREC_JACOBI, max_restarts=5)
+    ost = ostep.initial_state(ops.n)
+    oopt = ostep.StepOptions(vel_rtol=tol, pres_rtol=tol, lumped_correction=(correction == pm.STEP_LUMPED))
+    for k in range(3):
+        stats = pm.project_step(op, st, t1, t2, vel, pres, correction=correction, allow_not_converged=True)
+        rep = ostep.project_step(ops, ost, oopt)
+        u1, u2, u3, p = [t.cpu().numpy() for t in st.get()]
+        for nm, g, o in (("u1", u1, ost.u[0]), ("u2", u2, ost.u[1]), ("u3", u3, ost.u[2]), ("p", p, ost.p)):
+            scale = np.abs(o).max()
+            if scale == 0:
+                assert np.abs(g).max() == 0, (k, nm)
+                continue
+            assert np.abs(g - o).max() <= 1e-8 * scale, (name, k, nm, np.abs(g - o).max() / scale)
+        for c in range(3):
+            assert abs(stats[c].iters - rep.vel[c].iters) <= 2 + 2 * stats[c].outer_iters
+        assert st.step_index == k + 1
