@@ -28,7 +28,7 @@ if ROOT not in sys.path:
 
 METRIC = "PCG GB/s % of HBM peak; solves/s, p99 latency vs plain FP64 at 1e-8 residual"
 WORKLOAD = "ocean basin 512x512 columns x 32 sigma layers, one FP64 projection step from rest"
-CPU_WINDOW = 48     # columns per side of the oracle's bounded sample
+CPU_WINDOW = 96     # columns per side of the oracle's bounded sample (~20 s on one core)
 
 
 def _env_int(name, default):
@@ -140,7 +140,7 @@ def cpu_worker(steps: int, warmup: int):
     from oracle import fem, step
     basin = oracle_window_basin()
     ops = fem.assemble(basin)
-    opts = step.StepOptions(vel_rtol=1e-8, pres_rtol=1e-8)
+    opts = step.StepOptions(vel_rtol=1e-8, pres_rtol=1e-8, vel_prec="ic0", pres_prec="line")
     rates, secs = [], []
     for it in range(warmup + steps):
         st = step.initial_state(ops.n)
@@ -188,13 +188,13 @@ def run_ours(args):
         torch.cuda.set_device(0)
     dev_index = torch.cuda.current_device()
 
-    basin = ocean_basin()
+    basin = ocean_basin() if args.nx == 512 else ocean_basin(nx=args.nx, ny=args.nx, dx=1e4 * 512 / args.nx)
     op = pm.assemble_operator(basin)
     st = pm.State(op)
     t1 = torch.from_numpy(op.column_field(basin.theta[0])).cuda()
     t2 = torch.from_numpy(op.column_field(basin.theta[1])).cuda()
     vel = pm.Options(rtol=1e-8, prec=pm.PREC_IC0, max_iter=500000)
-    pres = pm.Options(rtol=1e-8, prec=pm.PREC_JACOBI, max_iter=500000)
+    pres = pm.Options(rtol=1e-8, prec=pm.PREC_LINE, max_iter=500000)
 
     def one_step():
         st.set(step_index=0)
@@ -224,7 +224,8 @@ def run_ours(args):
         dist.barrier()
     launches = pm.kernel_launch_count() - launches0
     ms_total = e0.elapsed_time(e1)
-    kt = {k: api.kernel_timing_get(k) for k in (api.KT_SPMV, api.KT_UPDATE, api.KT_PUPDATE, api.KT_IC0)}
+    kt = {k: api.kernel_timing_get(k) for k in (api.KT_SPMV, api.KT_UPDATE, api.KT_PUPDATE, api.KT_IC0,
+                                                 api.KT_LINE)}
     api.kernel_timing(False)
     clk = clocks.stop()
 
@@ -244,9 +245,10 @@ def run_ours(args):
         api.KT_UPDATE: n * (4 * 8 + 2 * 8),           # IC0 path: x, r, p, w read; x, r written
         api.KT_PUPDATE: n * (3 * 8 + 8) / 2,          # (r, z) dot + p update, two launches
         api.KT_IC0: n * (2 * 8 * 8 + 4 * 8) / 16,     # F (8 per row per sweep), r/y/z, per launch
+        api.KT_LINE: n * (8 + 3 * 8 + 8 + 8),         # r, 3 Thomas factors, z, m
     }
     names = {api.KT_SPMV: "k_cg_spmv", api.KT_UPDATE: "k_cg_update", api.KT_PUPDATE: "k_cg_rho+k_cg_pupd",
-             api.KT_IC0: "k_ic0_sweep"}
+             api.KT_IC0: "k_ic0_sweep", api.KT_LINE: "k_line_rho"}
     dom = max(kt, key=lambda k: kt[k][0])
     dom_ms, dom_launches = kt[dom]
     peak, peak_kind = measured_peaks()
@@ -317,7 +319,7 @@ def run_ours(args):
             "data": "synthetic (seeded ocean basin: smoothed-noise land mask, sum-of-Gaussians bathymetry)",
             "config": {"workload": WORKLOAD, "basin": basin.name, "nodes": n, "columns": op.ncols,
                        "velocity": "IC0-PCG x3 (multicolour), rtol 1e-8",
-                       "pressure": "Jacobi(DIAG)-PCG, zero-mean multiplier, rtol 1e-8",
+                       "pressure": "vertical-line block-Jacobi PCG, zero-mean multiplier, rtol 1e-8",
                        "correction": "lumped mass", "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": "operators 4.5 GB > L2, no flush needed"},
             "pct_hbm_peak": round(value / world / peak, 4),
@@ -359,6 +361,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-worker", action="store_true")
+    ap.add_argument("--nx", type=int, default=512,
+                    help="basin columns per side (512 = the benchmark workload; smaller for profiling)")
     args = ap.parse_args()
     if args.cpu_worker:
         cpu_worker(args.steps, args.warmup)

@@ -94,9 +94,12 @@ typedef enum pm_which {
 } pm_which;
 
 /* Preconditioners (Section 5 remark): IC0 is the paper's choice for the velocity and mass
- * systems (multicolour order, see DESIGN); JACOBI is the diagonal ("DIAG") and the labelled
- * fallback; NONE is plain CG. */
-enum { PM_PREC_JACOBI = 0, PM_PREC_IC0 = 1, PM_PREC_NONE = 2 };
+ * systems (zero fill, multicolour order: colour = (i&1) | (j&1)<<1 | (k&1)<<2); JACOBI is the
+ * diagonal ("DIAG") and the labelled fallback; NONE is plain CG. LINE is vertical-line block
+ * Jacobi -- each column's tridiagonal block of A solved exactly -- a labelled reading for the
+ * pressure system of a thin layered domain (the paper's "DIAG + LS CGS OPT" is not defined in
+ * it), not the paper's method. */
+enum { PM_PREC_JACOBI = 0, PM_PREC_IC0 = 1, PM_PREC_NONE = 2, PM_PREC_LINE = 3 };
 /* Arithmetic of the inner iteration. FP64 throughout, or FP32 (BF16) operator values with FP32
  * vectors inside PCG, FP64 dot products / alpha / beta, and FP64 outer iterative refinement on
  * the true residual until rtol is met. */
@@ -117,11 +120,13 @@ typedef struct pm_solve_stats {
   int32_t iters;              /* PCG iterations (summed over restarts / inner solves)       */
   int32_t outer_iters;        /* refinement steps (mixed precision), restarts (FP64)        */
   int32_t status;             /* PM_* of this solve                                         */
-  int32_t reserved;
+  int32_t first_pass_iters;   /* iterations until the recursive residual first met rtol    */
   double rel_residual_true;   /* ||b - A x|| / ||b|| in FP64 at exit                         */
   double rel_residual_rec;    /* recursive residual estimate at exit                        */
   double seconds;             /* host wall time of the call                                 */
   double bytes_moved;         /* algorithmic bytes (values, vectors) the iterations moved   */
+  double rel_residual_floor;  /* u || |A||x| + |b| ||_2 / ||b||_2, u = 2^-53: the relative
+                                 residual that rounding x to FP64 alone can cause           */
 } pm_solve_stats;
 
 typedef struct pm_operator_info {
@@ -214,7 +219,8 @@ enum { PM_KT_SPMV = 0,    /* SpMV + (p, Ap) reduction, one launch per PCG iterat
        PM_KT_UPDATE = 1,  /* x, r update + residual reductions                           */
        PM_KT_PUPDATE = 2, /* search-direction update (with the (r, z) reduction for IC0) */
        PM_KT_IC0 = 3,     /* the 16 IC0 colour sweeps of one preconditioner apply        */
-       PM_KT_COUNT = 4 };
+       PM_KT_LINE = 4,    /* the vertical-line solve fused with the (r, z) reduction     */
+       PM_KT_COUNT = 5 };
 int pm_kernel_timing(int32_t enable);
 int pm_kernel_timing_get(int32_t kind, double* total_ms, int64_t* launches);
 

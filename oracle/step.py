@@ -67,6 +67,8 @@ def _precond(A, kind: str, mesh: Mesh):
         return pcgm.ic0_preconditioner(A, mesh.colour)[0]
     if kind == "ic0_natural":
         return pcgm.ic0_preconditioner(A, None)[0]
+    if kind == "line":
+        return pcgm.line_preconditioner(A, mesh.nz)
     raise ValueError(kind)
 
 

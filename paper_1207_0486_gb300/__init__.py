@@ -9,7 +9,7 @@ from .api import (  # noqa: F401
     Operator, State, Options, SolveStats, PMError,
     assemble_operator, pcg_solve, project_step, operator_bytes, kernel_launch_count, load,
     OP_VEL_U1, OP_VEL_U2, OP_VEL_U3, OP_PRESSURE, OP_MASS, OP_VEL1_U1, OP_VEL1_U2, OP_VEL1_U3,
-    OP_GRAD_X, OP_GRAD_Y, OP_GRAD_Z, PREC_JACOBI, PREC_IC0, PREC_NONE, FP64, FP32_REFINE,
+    OP_GRAD_X, OP_GRAD_Y, OP_GRAD_Z, PREC_JACOBI, PREC_IC0, PREC_NONE, PREC_LINE, FP64, FP32_REFINE,
     BF16_REFINE, STEP_LUMPED, STEP_CONSISTENT, SLOT_OFFSETS, NBR_OFFSETS,
     PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_NOT_CONVERGED, PM_BREAKDOWN, PM_TIMEOUT,
     PM_DISCONNECTED,

@@ -21,7 +21,7 @@ PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_NOT_CONVERGED, PM_BREAKDOWN, PM_TIMEOU
 PM_WALL_WEST, PM_WALL_EAST, PM_WALL_SOUTH, PM_WALL_NORTH = 1, 2, 4, 8
 OP_VEL_U1, OP_VEL_U2, OP_VEL_U3, OP_PRESSURE, OP_MASS = 0, 1, 2, 3, 4
 OP_VEL1_U1, OP_VEL1_U2, OP_VEL1_U3, OP_GRAD_X, OP_GRAD_Y, OP_GRAD_Z = 5, 6, 7, 8, 9, 10
-PREC_JACOBI, PREC_IC0, PREC_NONE = 0, 1, 2
+PREC_JACOBI, PREC_IC0, PREC_NONE, PREC_LINE = 0, 1, 2, 3
 FP64, FP32_REFINE, BF16_REFINE = 0, 1, 2
 STEP_LUMPED, STEP_CONSISTENT = 0, 1
 
@@ -50,12 +50,12 @@ class SolveOpts(ctypes.Structure):
 
 class SolveStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("outer_iters", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("rel_residual_true", ctypes.c_double),
+                ("first_pass_iters", ctypes.c_int32), ("rel_residual_true", ctypes.c_double),
                 ("rel_residual_rec", ctypes.c_double), ("seconds", ctypes.c_double),
-                ("bytes_moved", ctypes.c_double)]
+                ("bytes_moved", ctypes.c_double), ("rel_residual_floor", ctypes.c_double)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class OperatorInfo(ctypes.Structure):
@@ -90,7 +90,7 @@ SIGNATURES = {
     "pm_kernel_timing_get": (_I, [ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
 }
 
-KT_SPMV, KT_UPDATE, KT_PUPDATE, KT_IC0 = 0, 1, 2, 3
+KT_SPMV, KT_UPDATE, KT_PUPDATE, KT_IC0, KT_LINE = 0, 1, 2, 3, 4
 
 
 def kernel_timing(enable: bool):

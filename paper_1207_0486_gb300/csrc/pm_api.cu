@@ -75,6 +75,7 @@ static void free_operator(pm_operator* op) {
     cudaFree(op->d_dinv[w]);
     cudaFree(op->d_dinv32[w]);
     cudaFree(op->ic0[w].F);
+    cudaFree(op->d_line[w]);
   }
   delete op;
 }

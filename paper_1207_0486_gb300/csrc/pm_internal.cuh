@@ -155,6 +155,8 @@ struct pm_operator {
   double* d_dinv[8] = {};           // Jacobi inverse diagonals per (op, mask)
   float* d_dinv32[8] = {};
   pm::Ic0Factor ic0[8];
+  double* d_line[8] = {};           // vertical-line factors per (op, mask): 3 x n, level-major
+  bool line_ok[8] = {};
   pm::SolveCtx* ctx = nullptr;
   double one_m = 0.0;
   int64_t device_bytes = 0;

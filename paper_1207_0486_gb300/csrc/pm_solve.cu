@@ -16,6 +16,7 @@
 // every few dozen iterations to see whether the solve has finished. Kernels of iterations
 // issued after convergence return at once (the device "done" flag), so the result is the same
 // as testing after every iteration.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <chrono>
@@ -164,14 +165,18 @@ __device__ __forceinline__ bool sc_done(const PcgScalars* sc) {
 
 // Row r of the (optionally masked) operator times x. MASKC >= 0: symmetric elimination of
 // component MASKC's Dirichlet set (identity row, zero column).
-template <int MASKC, typename TV, typename TX>
+template <int MASKC, typename TV, typename TX, bool ABS = false>
 __device__ __forceinline__ double row_dot(const Geom& g, const TV* __restrict__ val, const TX* __restrict__ x,
-                                          int64_t row, int col, int k, bool& is_dir) {
+                                          int64_t row, int col, int k, bool& is_dir, double* abs_sum = nullptr) {
   const int nz = g.nz;
   if (MASKC >= 0) {
     is_dir = is_dirichlet(g.colflag[col], k, nz, MASKC);
-    if (is_dir) return (double)x[row];
+    if (is_dir) {
+      if (ABS) *abs_sum = fabs((double)x[row]);
+      return (double)x[row];
+    }
   }
+  double asum = 0.0;
   int nb[NNBR];
   uint8_t fl[NNBR];
 #pragma unroll
@@ -187,8 +192,11 @@ __device__ __forceinline__ double row_dot(const Geom& g, const TV* __restrict__ 
     if (nb[q] < 0 || kk < 0 || kk >= nz) continue;
     if (MASKC >= 0 && is_dirichlet(fl[q], kk, nz, MASKC)) continue;
     const double a = (double)val[(int64_t)s * g.npad + row];
-    sum = fma(a, (double)x[(int64_t)nb[q] * nz + kk], sum);
+    const double xv = (double)x[(int64_t)nb[q] * nz + kk];
+    sum = fma(a, xv, sum);
+    if (ABS) asum += fabs(a * xv);
   }
+  if (ABS) *abs_sum = asum;
   return sum;
 }
 
@@ -239,20 +247,25 @@ __global__ void __launch_bounds__(TPB) k_cg_residual(Geom g, const double* __res
                                                      const double* __restrict__ bw, const double* __restrict__ x,
                                                      double* __restrict__ r, double rtol, double* partials,
                                                      PcgScalars* sc) {
-  double v[2] = {0.0, 0.0};
+  double v[3] = {0.0, 0.0, 0.0};
   for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < g.n;
        row += (int64_t)gridDim.x * blockDim.x) {
     const int col = (int)(row / g.nz);
     const int k = (int)(row - (int64_t)col * g.nz);
     bool d = false;
-    const double ax = row_dot<MASKC>(g, val, x, row, col, k, d);
+    double asum = 0.0;
+    const double ax = row_dot<MASKC, double, double, MODE == 1>(g, val, x, row, col, k, d, &asum);
     const double bi = bw[row];
     const double ri = bi - ax;
     r[row] = ri;
     v[0] = fma(bi, bi, v[0]);
     v[1] = fma(ri, ri, v[1]);
+    if (MODE == 1) {
+      const double f = asum + fabs(bi);
+      v[2] = fma(f, f, v[2]);
+    }
   }
-  if (grid_sum<2>(v, partials, &sc->count[1]) && threadIdx.x == 0) {
+  if (grid_sum<3>(v, partials, &sc->count[1]) && threadIdx.x == 0) {
     if (MODE == 0) {
       sc->bb = v[0];
       sc->rr = v[1];
@@ -263,6 +276,7 @@ __global__ void __launch_bounds__(TPB) k_cg_residual(Geom g, const double* __res
       sc->done = (v[0] == 0.0 || v[1] <= sc->tol2) ? 1 : 0;
     } else {
       sc->aux[0] = v[1];
+      sc->aux[1] = v[2];
     }
   }
 }
@@ -434,6 +448,163 @@ __global__ void __launch_bounds__(TPB) k_ic0_sweep(Geom g, CMap cm, const int32_
 }
 
 // Grid of the reduction kernels: at most MAX_GRID blocks (the size of the partials buffer).
+// ---- vertical-line block Jacobi ----------------------------------------------------------------
+// P = block diagonal of A made of each column's tridiagonal block (rows k, couplings k-1 / k+1
+// inside the column, the same Dirichlet elimination as A). Thomas factors per row, stored
+// level-major (index k * ncols + column) so that one thread per column reads them coalesced:
+//   lo_k = A[k, k-1],  w_k = 1 / (A[k, k] - lo_k cp_{k-1}),  cp_k = A[k, k+1] w_k.
+__global__ void k_line_factor(Geom g, const double* __restrict__ val, int maskc, double* __restrict__ F,
+                              int* __restrict__ breakdown) {
+  const int nz = g.nz;
+  const int64_t n = g.n;
+  for (int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; col < g.ncols;
+       col += (int64_t)gridDim.x * blockDim.x) {
+    const uint8_t fl = g.colflag[col];
+    double cprev = 0.0;
+    for (int k = 0; k < nz; ++k) {
+      const int64_t row = col * nz + k;
+      const bool di = maskc >= 0 && is_dirichlet(fl, k, nz, maskc);
+      const double d = di ? 1.0 : val[(int64_t)DIAG_SLOT * g.npad + row];
+      double lo = 0.0, up = 0.0;
+      if (k > 0 && !di && !(maskc >= 0 && is_dirichlet(fl, k - 1, nz, maskc))) lo = val[row];
+      if (k < nz - 1 && !di && !(maskc >= 0 && is_dirichlet(fl, k + 1, nz, maskc)))
+        up = val[2 * g.npad + row];
+      double piv = d - lo * cprev;
+      if (!(piv > 0.0)) {
+        atomicExch(breakdown, 1);
+        piv = 1.0;
+      }
+      const double w = 1.0 / piv;
+      const double cp = up * w;
+      const int64_t li = (int64_t)k * g.ncols + col;
+      F[li] = lo;
+      F[n + li] = w;
+      F[2 * n + li] = cp;
+      cprev = cp;
+    }
+  }
+}
+
+constexpr int LINE_COLS = 64;
+constexpr int LINE_TPB = 128;
+
+// z = P^{-1} r for whole columns staged in shared memory, fused with the (r, z) [m'z, 1'r]
+// reductions and the beta update (as k_cg_rho).
+template <int PROJ>
+__global__ void __launch_bounds__(LINE_TPB) k_line_rho(Geom g, const double* __restrict__ F,
+                                                       const double* __restrict__ r, double* __restrict__ z,
+                                                       const double* __restrict__ m, double* partials,
+                                                       PcgScalars* sc, int is_first) {
+  extern __shared__ double smem[];
+  if (!is_first && sc_done(sc)) return;
+  const int nz = g.nz, ld = nz + 1;
+  double* sr = smem;
+  double* sz = smem + LINE_COLS * ld;
+  const int64_t n = g.n;
+  const int64_t ntiles = (g.ncols + LINE_COLS - 1) / LINE_COLS;
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t c0 = tile * LINE_COLS;
+    const int cc = (int)min((int64_t)LINE_COLS, (int64_t)g.ncols - c0);
+    const int64_t row0 = c0 * nz;
+    const int rows = cc * nz;
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) sr[(i / nz) * ld + i % nz] = r[row0 + i];
+    __syncthreads();
+    if ((int)threadIdx.x < cc) {
+      const int64_t col = c0 + threadIdx.x;
+      const int base = threadIdx.x * ld;
+      double y = 0.0;
+      for (int k = 0; k < nz; ++k) {
+        const int64_t li = (int64_t)k * g.ncols + col;
+        y = (sr[base + k] - F[li] * y) * F[n + li];
+        sz[base + k] = y;
+      }
+      double zn = sz[base + nz - 1];
+      for (int k = nz - 2; k >= 0; --k) {
+        const int64_t li = (int64_t)k * g.ncols + col;
+        zn = fma(-F[2 * n + li], zn, sz[base + k]);
+        sz[base + k] = zn;
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+      const int si = (i / nz) * ld + i % nz;
+      const double zi = sz[si], ri = sr[si];
+      z[row0 + i] = zi;
+      v[0] = fma(ri, zi, v[0]);
+      if (PROJ) {
+        v[1] = fma(m[row0 + i], zi, v[1]);
+        v[2] += ri;
+      }
+    }
+    __syncthreads();
+  }
+  if (grid_sum<3>(v, partials, &sc->count[2]) && threadIdx.x == 0) {
+    const double c = PROJ ? v[1] / sc->one_m : 0.0;
+    const double rho_new = v[0] - c * v[2];
+    sc->proj_c = c;
+    if (is_first) {
+      sc->rho = rho_new;
+      sc->beta = 0.0;
+    } else {
+      sc->beta = rho_new / sc->rho;
+      sc->rho = rho_new;
+    }
+    if (!(rho_new > 0.0) || !isfinite(rho_new)) {
+      if (!sc->done) {
+        sc->status = PM_BREAKDOWN;
+        sc->done = 1;
+      }
+    }
+  }
+}
+
+void line_apply_rho(pm_operator* op, int which, bool proj, int is_first, cudaStream_t s) {
+  SolveCtx* c = op->ctx;
+  Geom g = geom_of(op);
+  const int64_t ntiles = (op->ncols + LINE_COLS - 1) / LINE_COLS;
+  int grid = (int)std::min<int64_t>(ntiles, std::min<int64_t>((int64_t)op->num_sms * 8, MAX_GRID));
+  if (grid < 1) grid = 1;
+  const size_t smem = 2 * (size_t)LINE_COLS * (op->nz + 1) * sizeof(double);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_line_rho<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_line_rho<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  if (proj)
+    k_line_rho<1><<<grid, LINE_TPB, smem, s>>>(g, op->d_line[which], c->r, c->z, op->d_m, c->partials, c->sc, is_first);
+  else
+    k_line_rho<0><<<grid, LINE_TPB, smem, s>>>(g, op->d_line[which], c->r, c->z, op->d_m, c->partials, c->sc, is_first);
+  count_launch();
+}
+
+int line_factor(pm_operator* op, int which, cudaStream_t s) {
+  if (op->line_ok[which]) return PM_OK;
+  int st;
+  if (!op->d_line[which]) {
+    if ((st = cuda_check(cudaMalloc((void**)&op->d_line[which], 3 * (size_t)op->n * sizeof(double)), "cudaMalloc line")))
+      return st;
+    op->device_bytes += 3 * op->n * 8;
+  }
+  int* d_bd = nullptr;
+  if ((st = cuda_check(cudaMallocAsync((void**)&d_bd, sizeof(int), s), "cudaMallocAsync"))) return st;
+  cudaMemsetAsync(d_bd, 0, sizeof(int), s);
+  Geom g = geom_of(op);
+  int grid = (int)std::min<int64_t>((op->ncols + 127) / 128, (int64_t)op->num_sms * 16);
+  if (grid < 1) grid = 1;
+  k_line_factor<<<grid, 128, 0, s>>>(g, op->d_val[which_valset(which)], which_mask(which), op->d_line[which], d_bd);
+  count_launch();
+  int h = 0;
+  st = cuda_check(cudaMemcpyAsync(&h, d_bd, sizeof(int), cudaMemcpyDeviceToHost, s), "memcpy");
+  if (!st) st = cuda_check(cudaStreamSynchronize(s), "line factor");
+  cudaFreeAsync(d_bd, s);
+  if (st) return st;
+  if (h) return set_error(PM_BREAKDOWN, "vertical-line preconditioner: non-positive pivot");
+  op->line_ok[which] = true;
+  return cuda_check(cudaGetLastError(), "k_line_factor");
+}
+
 int grid_for(int64_t n, int threads, int sms) {
   int64_t gsz = (n + threads - 1) / threads;
   int64_t cap = (int64_t)sms * 8;
@@ -501,16 +672,31 @@ int ensure_ctx(pm_operator* op) {
 }
 
 template <int MASKC>
-void launch_iter(pm_operator* op, int which, const double* val, double* x, bool proj, bool ic0,
+void launch_iter(pm_operator* op, int which, const double* val, double* x, bool proj, int prec,
                  const double* dinv, cudaStream_t s) {
   SolveCtx* c = op->ctx;
   Geom g = geom_of(op);
   const int G = grid_for(op->n, TPB, op->num_sms);
+  const bool ic0 = prec == PM_PREC_IC0;
   {
     KtScope t(PM_KT_SPMV, 1, s);
     k_cg_spmv<MASKC><<<G, TPB, 0, s>>>(g, val, c->p, c->w, c->partials, c->sc);
   }
-  if (!ic0) {
+  if (prec == PM_PREC_LINE) {
+    {
+      KtScope t(PM_KT_UPDATE, 1, s);
+      k_cg_update<0, 0><<<G, TPB, 0, s>>>(op->n, x, c->r, c->p, c->w, dinv, op->d_m, c->partials, c->sc);
+    }
+    {
+      KtScope t(PM_KT_LINE, 1, s);
+      line_apply_rho(op, which, proj, 0, s);
+    }
+    {
+      KtScope t(PM_KT_PUPDATE, 1, s);
+      k_cg_pupd<1><<<G, TPB, 0, s>>>(op->n, c->r, dinv, c->z, c->p, c->sc, 0);
+    }
+    count_launch(2);
+  } else if (!ic0) {
     {
       KtScope t(PM_KT_UPDATE, 1, s);
       if (proj) {
@@ -562,10 +748,16 @@ void launch_residual(pm_operator* op, const double* val, const double* bw, const
 
 // z, p, rho from the current r (first step or restart). The kernels run even when "done" is
 // set by the setup so that a zero initial residual still leaves consistent scalars.
-void launch_first(pm_operator* op, int which, bool proj, bool ic0, const double* dinv, cudaStream_t s) {
+void launch_first(pm_operator* op, int which, bool proj, int prec, const double* dinv, cudaStream_t s) {
   SolveCtx* c = op->ctx;
   const int G = grid_for(op->n, TPB, op->num_sms);
-  if (ic0) {
+  if (prec == PM_PREC_LINE) {
+    line_apply_rho(op, which, proj, 1, s);
+    k_cg_pupd<1><<<G, TPB, 0, s>>>(op->n, c->r, dinv, c->z, c->p, c->sc, 1);
+    count_launch(1);
+    return;
+  }
+  if (prec == PM_PREC_IC0) {
     ic0_apply(op, which, c->r, c->z, c->sc, 0, s);
     if (proj) k_cg_rho<1, 1><<<G, TPB, 0, s>>>(op->n, c->r, dinv, c->z, op->d_m, c->partials, c->sc, 1);
     else k_cg_rho<0, 1><<<G, TPB, 0, s>>>(op->n, c->r, dinv, c->z, op->d_m, c->partials, c->sc, 1);
@@ -596,10 +788,13 @@ int read_scalars(SolveCtx* c, cudaStream_t s) {
 
 // Algorithmic bytes of one PCG iteration per row (FP64): SpMV 15 values + p read + w write,
 // update x, r read/write + p, w, dinv read, p-update r, dinv, p read + p write.
-double bytes_per_iter(const pm_operator* op, bool ic0) {
+// IC0 adds the factor (8 slots read per row per sweep, two sweeps) and r / y / z traffic;
+// LINE adds r read, 3 factors, z write (its (r, z) reduction is fused).
+double bytes_per_iter(const pm_operator* op, int prec) {
   const double n = (double)op->n;
   double b = n * (15 * 8 + 8 + 8) + n * (5 * 8 + 2 * 8) + n * (3 * 8 + 8);
-  if (ic0) b += n * (2 * 8 * 8 + 4 * 8);
+  if (prec == PM_PREC_IC0) b += n * (2 * 8 * 8 + 4 * 8);
+  if (prec == PM_PREC_LINE) b += n * (8 + 3 * 8 + 8);
   return b;
 }
 
@@ -610,6 +805,7 @@ int pcg_run(pm_operator* op, int which, const double* b, double* x, const pm_sol
   SolveCtx* c = op->ctx;
   const bool proj = which == PM_OP_PRESSURE;
   const bool ic0 = o->prec == PM_PREC_IC0;
+  const int prec = o->prec;
   const double* val = op->d_val[which_valset(which)];
   int st;
   // Preconditioner set-up.
@@ -636,6 +832,7 @@ int pcg_run(pm_operator* op, int which, const double* b, double* x, const pm_sol
       if (bd) return set_error(PM_BREAKDOWN, "IC0 pivot failure after the shift limit");
     }
   }
+  if (prec == PM_PREC_LINE && (st = line_factor(op, which, s))) return st;
   // Right-hand side and initial guess.
   const int G = grid_for(op->n, TPB, op->num_sms);
   PcgScalars init;
@@ -654,11 +851,12 @@ int pcg_run(pm_operator* op, int which, const double* b, double* x, const pm_sol
     count_launch();
   }
   launch_residual<MASKC>(op, val, bw, x, o->rtol, 0, s);
-  launch_first(op, which, proj, ic0, dinv, s);
+  launch_first(op, which, proj, prec, dinv, s);
   if ((st = read_scalars(c, s))) return st;
   int restarts = 0;
+  int first_pass = 0;
   int status = PM_OK;
-  double rel_true = 0.0;
+  double rel_true = 0.0, rel_floor = 0.0;
   if (c->sc_host->zero_rhs) {
     k_fill<<<G, TPB, 0, s>>>(x, op->n, 0.0);
     count_launch();
@@ -671,17 +869,22 @@ int pcg_run(pm_operator* op, int which, const double* b, double* x, const pm_sol
         // the device stops itself at max_iter; this bound only guards the host loop
         if (issued > (int64_t)o->max_iter + 4096)
           return set_error(PM_ECUDA, "PCG driver: device never reported completion");
-        for (int it = 0; it < chunk; ++it) launch_iter<MASKC>(op, which, val, x, proj, ic0, dinv, s);
+        for (int it = 0; it < chunk; ++it) launch_iter<MASKC>(op, which, val, x, proj, prec, dinv, s);
         issued += chunk;
         if ((st = read_scalars(c, s))) return st;
         if (chunk < 64) chunk *= 2;
       }
       status = c->sc_host->status;
+      if (restarts == 0) first_pass = c->sc_host->iter;
       // true residual
       launch_residual<MASKC>(op, val, bw, x, o->rtol, 1, s);
       if ((st = read_scalars(c, s))) return st;
       rel_true = std::sqrt(c->sc_host->aux[0] / c->sc_host->bb);
-      if (status != PM_OK || rel_true <= o->rtol || restarts >= o->max_restarts ||
+      rel_floor = std::ldexp(1.0, -53) * std::sqrt(c->sc_host->aux[1] / c->sc_host->bb);
+      // Accepted when the true residual meets rtol, or when it is already below the floor that
+      // rounding x to FP64 alone produces (backward error at the unit roundoff): restarts could
+      // not lower it further.
+      if (status != PM_OK || rel_true <= std::max(o->rtol, rel_floor) || restarts >= o->max_restarts ||
           c->sc_host->iter >= o->max_iter)
         break;
       ++restarts;
@@ -690,10 +893,10 @@ int pcg_run(pm_operator* op, int which, const double* b, double* x, const pm_sol
       hs->done = 0;
       hs->rr = hs->aux[0];
       if ((st = cuda_check(cudaMemcpyAsync(c->sc, hs, sizeof(PcgScalars), cudaMemcpyHostToDevice, s), "scalars"))) return st;
-      launch_first(op, which, proj, ic0, dinv, s);
+      launch_first(op, which, proj, prec, dinv, s);
       if ((st = read_scalars(c, s))) return st;
     }
-    if (status == PM_OK && rel_true > o->rtol) status = PM_NOT_CONVERGED;
+    if (status == PM_OK && rel_true > std::max(o->rtol, rel_floor)) status = PM_NOT_CONVERGED;
   }
   if (proj) {
     // keep m'x = 0 exactly as returned result
@@ -706,10 +909,12 @@ int pcg_run(pm_operator* op, int which, const double* b, double* x, const pm_sol
   if (stats) {
     stats->iters = h->iter;
     stats->outer_iters = restarts;
+    stats->first_pass_iters = first_pass;
+    stats->rel_residual_floor = rel_floor;
     stats->status = status;
     stats->rel_residual_true = h->zero_rhs ? 0.0 : rel_true;
     stats->rel_residual_rec = h->zero_rhs ? 0.0 : std::sqrt(h->rr / h->bb);
-    stats->bytes_moved = h->iter * bytes_per_iter(op, ic0);
+    stats->bytes_moved = h->iter * bytes_per_iter(op, prec);
     stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   if ((st = cuda_check(cudaGetLastError(), "pcg kernels"))) return st;
@@ -740,7 +945,7 @@ int spmv(pm_operator* op, int which, const double* x, double* y, cudaStream_t s)
 int pcg_solve(pm_operator* op, int which, const double* b, double* x, const pm_solve_opts* o,
               pm_solve_stats* st, cudaStream_t s) {
   if (!which_symmetric(which)) return set_error(PM_EINVAL, "pcg needs a symmetric operator");
-  if (o->prec < 0 || o->prec > PM_PREC_NONE) return set_error(PM_EINVAL, "unknown preconditioner");
+  if (o->prec < 0 || o->prec > PM_PREC_LINE) return set_error(PM_EINVAL, "unknown preconditioner");
   if (!(o->rtol > 0.0) || o->max_iter < 0) return set_error(PM_EINVAL, "rtol must be > 0, max_iter >= 0");
   int r = ensure_ctx(op);
   if (r) return r;

@@ -186,3 +186,43 @@ def test_step_consistent_vs_lumped_correction():
     np.testing.assert_allclose(s1.p, s2.p, rtol=1e-9, atol=1e-12 * np.abs(s1.p).max())
     d = np.linalg.norm(s1.u - s2.u) / np.linalg.norm(s2.u)
     assert d < 0.5
+
+
+def _line_block_matrix(A, nz):
+    """The block diagonal of A made of each column's entries with |dk| <= 1 (scipy, no Thomas)."""
+    C = A.tocoo()
+    keep = (C.row // nz == C.col // nz) & (np.abs(C.row - C.col) <= 1)
+    return sp.csr_matrix((C.data[keep], (C.row[keep], C.col[keep])), shape=A.shape)
+
+
+@pytest.mark.parametrize("which", ["vel", "pres"])
+def test_line_preconditioner_solves_the_column_blocks(which, basin):
+    nz = basin.mesh.nz
+    A = basin.A_u(0) if which == "vel" else basin.K_I
+    P = _line_block_matrix(A, nz)
+    apply = pcg.line_preconditioner(A, nz)
+    r = random_vector(basin.n, 8)
+    z = apply(r)
+    assert np.linalg.norm(P @ z - r) <= 1e-12 * np.linalg.norm(r)
+    z2 = spla.spsolve(P.tocsc(), r)
+    assert np.linalg.norm(z - z2) <= 1e-10 * np.linalg.norm(z2)
+
+
+def test_line_preconditioner_is_exact_on_a_block_diagonal_matrix(basin):
+    """If A has no coupling between columns, line-preconditioned CG converges in one step."""
+    P = _line_block_matrix(basin.A_u(2), basin.mesh.nz)
+    b = _rhs(basin, 2, 9)
+    res = pcg.pcg(P, b, rtol=1e-12, precond=pcg.line_preconditioner(P, basin.mesh.nz))
+    assert res.iters == 1
+
+
+def test_line_iteration_counts_match_scipy_cg():
+    ops = fem.assemble(box_basin())
+    for A, c in ((ops.A_u(0, True), 0), (ops.K_I, None)):
+        b = _rhs(ops, c, 41)
+        if c is None:
+            b = b - b.sum() / ops.m.sum() * ops.m
+        P = pcg.line_preconditioner(A, ops.mesh.nz)
+        res = pcg.pcg(A, b, rtol=1e-9, precond=P, max_restarts=0)
+        it = _scipy_cg_iters(A, b, P, 1e-9)
+        assert abs(res.first_pass_iters - it) <= 1, (res.first_pass_iters, it)
