@@ -304,7 +304,7 @@ def run_ours(args):
         try:
             w = run_cpu_oracle(1, 0)
             cpu = {"value": round(w["gbs"], 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-                   "sample": f"one oracle projection step (FP64, IC0 velocity, Jacobi pressure, rtol 1e-8) "
+                   "sample": f"one oracle projection step (FP64, IC0 velocity, line-preconditioned pressure, rtol 1e-8) "
                              f"on {w['sample']} ({w['n']} nodes), {w['seconds']:.1f} s",
                    "seconds_per_step": round(w["seconds"], 2)}
         except Exception as ex:  # the GPU number stands on its own
