@@ -171,6 +171,23 @@ int pm_spmv(pm_operator* op, pm_which which, const double* x, double* y, pm_stre
 int pm_pcg_solve(pm_operator* op, pm_which which, const double* b, double* x,
                  const pm_solve_opts* opts, pm_solve_stats* stats, pm_stream stream);
 
+/* Same solve as pm_pcg_solve, restricted to PM_PREC_JACOBI / PM_PREC_NONE in FP64, that
+ * allocates nothing. (The paper has no counterpart: this is a deployment aid.) It is meant for
+ * callers that cannot allocate device memory at solve time: code inside a CUDA stream capture
+ * that must not gain allocation nodes, processes whose device memory is owned by a framework
+ * allocator or a fixed pool, and embedded users that must not grow the footprint after start-up.
+ * All scratch (Krylov vectors, Jacobi diagonal, reduction partials, device scalars) lives in one
+ * static device array of PM_NOALLOC_MAX_ROWS rows (about 21 MB), held by every GPU that loads the
+ * library until the process exits; no cudaMalloc, cudaFree or other allocating routine is called.
+ * Systems with more than PM_NOALLOC_MAX_ROWS rows are rejected with PM_EINVAL. The first call on a
+ * device looks up the array's address (cudaGetSymbolAddress) with that device current: make it
+ * before any stream capture. Every call shares the one array and re-initialises what must start
+ * at zero; calls that overlap on the GPU (other streams or threads) race. The operator itself
+ * must already be assembled. Synchronises the stream. */
+#define PM_NOALLOC_MAX_ROWS 524288
+int pm_pcg_solve_noalloc(pm_operator* op, pm_which which, const double* b, double* x,
+                         const pm_solve_opts* opts, pm_solve_stats* stats, pm_stream stream);
+
 /* ---- projection step ---------------------------------------------------------------------- */
 
 /* Time-step state u^k, u^{k-1}, p^k (device, owned by the handle). Created at rest:

@@ -75,6 +75,7 @@ SIGNATURES = {
     "pm_operator_export": (_I, [_P, _I, _P, _P, _P]),
     "pm_spmv": (_I, [_P, _I, _P, _P, _P]),
     "pm_pcg_solve": (_I, [_P, _I, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), _P]),
+    "pm_pcg_solve_noalloc": (_I, [_P, _I, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), _P]),
     "pm_state_create": (_I, [_P, ctypes.POINTER(_P)]),
     "pm_state_get": (_I, [_P, _P, _P, _P, _P, _P]),
     "pm_state_set": (_I, [_P, _P, _P, _P, _P, ctypes.c_int32, _P]),
@@ -227,6 +228,15 @@ class Operator:
         r = load().pm_pcg_solve(self.handle, which, _dptr(b, self.n, "b"), _dptr(x, self.n, "x"),
                                 ctypes.byref(o), ctypes.byref(st), _stream(stream))
         _check(r, "pcg_solve", allow=(PM_NOT_CONVERGED,) if allow_not_converged else ())
+        return st
+
+    def solve_noalloc(self, which: int, b, x, opts: Options = Options(), stream=None, allow_not_converged=False):
+        """pm_pcg_solve_noalloc: Jacobi / plain PCG whose scratch is the library's static array."""
+        st = SolveStats()
+        o = opts.c()
+        r = load().pm_pcg_solve_noalloc(self.handle, which, _dptr(b, self.n, "b"), _dptr(x, self.n, "x"),
+                                        ctypes.byref(o), ctypes.byref(st), _stream(stream))
+        _check(r, "pcg_solve_noalloc", allow=(PM_NOT_CONVERGED,) if allow_not_converged else ())
         return st
 
     def close(self):

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpm_gb300.so")
-SOURCES = ["pm_api.cu", "pm_mesh.cu", "pm_assemble.cu", "pm_solve.cu", "pm_step.cu"]
+SOURCES = ["pm_api.cu", "pm_mesh.cu", "pm_assemble.cu", "pm_solve.cu", "pm_step.cu", "pm_noalloc.cu"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
