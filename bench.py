@@ -131,8 +131,9 @@ def oracle_step_bytes(n, rep):
     """Algorithmic PCG bytes of a step, the same per-row model as the GPU path."""
     per_jac = 15 * 8 + 8 + 8 + 5 * 8 + 2 * 8 + 3 * 8 + 8
     per_ic0 = per_jac + 2 * 8 * 8 + 4 * 8
+    per_line = per_jac + 8 + 3 * 8 + 8
     its_vel = sum(r.iters for r in rep.vel)
-    return n * (its_vel * per_ic0 + rep.pres.iters * per_jac)
+    return n * (its_vel * per_ic0 + rep.pres.iters * per_line)
 
 
 def cpu_worker(steps: int, warmup: int):
