@@ -300,6 +300,42 @@ def run_ours(args):
                "h2d_bytes_per_step": 2 * op.ncols * 8, "d2h_bytes_per_step": 4 * n * 8,
                "ms_per_step": round(ms_e2e, 3)}
 
+    # the same step with mixed precision (form 1): FP32 / BF16 operator values and inner PCG,
+    # FP64 dots, alpha/beta and outer refinement to the same 1e-8 rule; error vs the FP64 step
+    mixed = {}
+    if not args.no_mixed:
+        ref = [t.clone() for t in st.get()]
+        for label, prc in (("fp32", pm.FP32_REFINE), ("bf16", pm.BF16_REFINE)):
+            vm = pm.Options(rtol=1e-8, prec=pm.PREC_IC0, precision=prc, max_iter=500000)
+            pmo = pm.Options(rtol=1e-8, prec=pm.PREC_LINE, precision=prc, max_iter=500000)
+
+            def mstep():
+                st.set(step_index=0)
+                return pm.project_step(op, st, t1, t2, vm, pmo)
+            mstep()
+            torch.cuda.synchronize()
+            k_m = max(2, min(args.steps, 3))
+            g0 = torch.cuda.Event(enable_timing=True)
+            g1 = torch.cuda.Event(enable_timing=True)
+            g0.record()
+            for _ in range(k_m):
+                ms_stats = mstep()
+            g1.record()
+            torch.cuda.synchronize()
+            ms_m = g0.elapsed_time(g1) / k_m
+            got = st.get()
+            errs = {}
+            for nm, g, o in zip(("u", "v", "w", "p"), got, ref):
+                scale = float(o.abs().max())
+                errs[nm] = 0.0 if scale == 0 else float((g - o).abs().max() / scale)
+            mixed[label] = {"ms_per_step": round(ms_m, 3), "solves_per_s": round(solves_step / (ms_m * 1e-3), 3),
+                            "speedup_vs_fp64_step": round(ms_step / ms_m, 3),
+                            "pcg_gbs": round(sum(s.bytes_moved for s in ms_stats[:4]) / (ms_m * 1e-3) / 1e9, 1),
+                            "inner_iters": [int(s.iters) for s in ms_stats[:4]],
+                            "outer_iters": [int(s.outer_iters) for s in ms_stats[:4]],
+                            "rel_residual_true": [float(f"{s.rel_residual_true:.3e}") for s in ms_stats[:4]],
+                            "per_field_max_rel_err_vs_fp64": {k: float(f"{v:.3e}") for k, v in errs.items()}}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
@@ -328,6 +364,7 @@ def run_ours(args):
             "iters": [int(s.iters) for s in last[:4]],
             "rel_residual_true": [float(f"{s.rel_residual_true:.3e}") for s in last[:4]],
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "mixed_precision": mixed,
             "clocks": clk,
         }
         print(json.dumps(line))
@@ -361,6 +398,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--cpu-worker", action="store_true")
     ap.add_argument("--nx", type=int, default=512,
                     help="basin columns per side (512 = the benchmark workload; smaller for profiling)")

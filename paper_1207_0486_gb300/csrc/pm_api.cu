@@ -76,6 +76,8 @@ static void free_operator(pm_operator* op) {
     cudaFree(op->d_dinv32[w]);
     cudaFree(op->ic0[w].F);
     cudaFree(op->d_line[w]);
+    cudaFree(op->d_line32[w]);
+    cudaFree(op->d_ic0_32[w]);
   }
   delete op;
 }
@@ -282,7 +284,6 @@ int pm_spmv(pm_operator* op, pm_which which, const double* x, double* y, pm_stre
 int pm_pcg_solve(pm_operator* op, pm_which which, const double* b, double* x,
                  const pm_solve_opts* opts, pm_solve_stats* stats, pm_stream stream) {
   if (!op || !b || !x || !opts) return set_error(PM_EINVAL, "null argument");
-  if (opts->precision != PM_FP64) return set_error(PM_EINVAL, "this build solves in FP64 only");
   return pcg_solve(op, (int)which, b, x, opts, stats, (cudaStream_t)stream);
 }
 
@@ -349,8 +350,6 @@ int pm_project_step(pm_operator* op, pm_state* st, const double* theta1, const d
                     const pm_solve_opts* vel, const pm_solve_opts* pres, int32_t correction,
                     pm_solve_stats* stats, pm_stream stream) {
   if (!op || !st || !vel || !pres || st->op != op) return set_error(PM_EINVAL, "bad argument");
-  if (vel->precision != PM_FP64 || pres->precision != PM_FP64)
-    return set_error(PM_EINVAL, "this build solves in FP64 only");
   if (correction != PM_STEP_LUMPED && correction != PM_STEP_CONSISTENT)
     return set_error(PM_EINVAL, "unknown correction");
   return project_step(op, st, theta1, theta2, vel, pres, correction, stats, (cudaStream_t)stream);

@@ -157,6 +157,8 @@ struct pm_operator {
   pm::Ic0Factor ic0[8];
   double* d_line[8] = {};           // vertical-line factors per (op, mask): 3 x n, level-major
   bool line_ok[8] = {};
+  float* d_line32[8] = {};          // FP32 copies for mixed-precision inner solves
+  float* d_ic0_32[8] = {};
   pm::SolveCtx* ctx = nullptr;
   double one_m = 0.0;
   int64_t device_bytes = 0;

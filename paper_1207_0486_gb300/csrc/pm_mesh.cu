@@ -86,7 +86,8 @@ int build_host_mesh(const pm_mesh_desc* d, const double* coriolis, HostMesh* out
     }
   const int ncols = (int)m.col_i.size();
   m.ncols = ncols;
-  if ((int64_t)ncols * nz > ((int64_t)1 << 31) - 64) return set_error(PM_EINVAL, "too many nodes");
+  // Kernels index the 15-slot value arrays with 32-bit integers: 15 * n_pad must stay < 2^31.
+  if ((int64_t)ncols * nz > ((int64_t)1 << 27)) return set_error(PM_EINVAL, "too many nodes (limit 2^27 rows)");
   m.nbr.assign((size_t)ncols * NNBR, -1);
   m.depth.resize(ncols);
   m.cellmask.resize(ncols);

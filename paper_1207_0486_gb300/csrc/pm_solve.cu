@@ -16,10 +16,13 @@
 // every few dozen iterations to see whether the solve has finished. Kernels of iterations
 // issued after convergence return at once (the device "done" flag), so the result is the same
 // as testing after every iteration.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <chrono>
+#include <type_traits>
 
 #include "pm_internal.cuh"
 
@@ -31,6 +34,10 @@ struct SolveCtx {
   double* partials = nullptr;
   PcgScalars* sc = nullptr;
   PcgScalars* sc_host = nullptr;
+  // mixed precision (allocated on first use)
+  float *r32 = nullptr, *p32 = nullptr, *w32 = nullptr, *z32 = nullptr, *d32 = nullptr;
+  PcgScalars* sc_in = nullptr;
+  PcgScalars* sc_in_host = nullptr;
 };
 
 struct ColourMap;  // pm_assemble.cu
@@ -165,36 +172,46 @@ __device__ __forceinline__ bool sc_done(const PcgScalars* sc) {
 
 // Row r of the (optionally masked) operator times x. MASKC >= 0: symmetric elimination of
 // component MASKC's Dirichlet set (identity row, zero column).
+// Branch-free: all 15 value loads are unconditional (absent slots hold 0), an absent or
+// eliminated neighbour reads x[row] and multiplies a selected 0, so every load of a row can be
+// in flight at once. 32-bit indices: the library caps n so that 15 * n_pad < 2^31.
 template <int MASKC, typename TV, typename TX, bool ABS = false>
 __device__ __forceinline__ double row_dot(const Geom& g, const TV* __restrict__ val, const TX* __restrict__ x,
-                                          int64_t row, int col, int k, bool& is_dir, double* abs_sum = nullptr) {
+                                          int row, int col, int k, bool& is_dir, double* abs_sum = nullptr) {
   const int nz = g.nz;
-  if (MASKC >= 0) {
-    is_dir = is_dirichlet(g.colflag[col], k, nz, MASKC);
-    if (is_dir) {
-      if (ABS) *abs_sum = fabs((double)x[row]);
-      return (double)x[row];
-    }
-  }
-  double asum = 0.0;
+  const int npad = (int)g.npad;
   int nb[NNBR];
   uint8_t fl[NNBR];
+  nb[0] = col;
 #pragma unroll
-  for (int q = 0; q < NNBR; ++q) {
-    nb[q] = q == 0 ? col : __ldg(g.nbr + (int64_t)col * NNBR + q);
-    if (MASKC >= 0) fl[q] = nb[q] >= 0 ? __ldg(g.colflag + nb[q]) : 0;
+  for (int q = 1; q < NNBR; ++q) nb[q] = __ldg(g.nbr + col * NNBR + q);
+  if (MASKC >= 0) {
+#pragma unroll
+    for (int q = 0; q < NNBR; ++q) fl[q] = __ldg(g.colflag + (nb[q] >= 0 ? nb[q] : col));
   }
-  double sum = 0.0;
+  TV a[NSLOT];
+#pragma unroll
+  for (int s = 0; s < NSLOT; ++s) a[s] = __ldg(val + s * npad + row);
+  double sum = 0.0, asum = 0.0;
 #pragma unroll
   for (int s = 0; s < NSLOT; ++s) {
     const int q = slot_q(s);
     const int kk = k + slot_dk(s);
-    if (nb[q] < 0 || kk < 0 || kk >= nz) continue;
-    if (MASKC >= 0 && is_dirichlet(fl[q], kk, nz, MASKC)) continue;
-    const double a = (double)val[(int64_t)s * g.npad + row];
-    const double xv = (double)x[(int64_t)nb[q] * nz + kk];
-    sum = fma(a, xv, sum);
-    if (ABS) asum += fabs(a * xv);
+    bool ok = nb[q] >= 0;
+    if (slot_dk(s) < 0) ok = ok && kk >= 0;
+    if (slot_dk(s) > 0) ok = ok && kk < nz;
+    if (MASKC >= 0) ok = ok && !is_dirichlet(fl[q], kk, nz, MASKC);
+    const double xv = (double)x[ok ? nb[q] * nz + kk : row];
+    const double av = ok ? (double)a[s] : 0.0;
+    sum = fma(av, xv, sum);
+    if (ABS) asum += fabs(av * xv);
+  }
+  if (MASKC >= 0) {
+    is_dir = is_dirichlet(fl[0], k, nz, MASKC);
+    if (is_dir) {
+      sum = (double)x[row];
+      asum = fabs(sum);
+    }
   }
   if (ABS) *abs_sum = asum;
   return sum;
@@ -203,10 +220,10 @@ __device__ __forceinline__ double row_dot(const Geom& g, const TV* __restrict__ 
 template <int MASKC>
 __global__ void __launch_bounds__(TPB) k_spmv(Geom g, const double* __restrict__ val,
                                               const double* __restrict__ x, double* __restrict__ y) {
-  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < g.n;
-       row += (int64_t)gridDim.x * blockDim.x) {
-    const int col = (int)(row / g.nz);
-    const int k = (int)(row - (int64_t)col * g.nz);
+  const int n = (int)g.n;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
+    const int col = row / g.nz;
+    const int k = row - col * g.nz;
     bool d = false;
     y[row] = row_dot<MASKC>(g, val, x, row, col, k, d);
   }
@@ -248,10 +265,10 @@ __global__ void __launch_bounds__(TPB) k_cg_residual(Geom g, const double* __res
                                                      double* __restrict__ r, double rtol, double* partials,
                                                      PcgScalars* sc) {
   double v[3] = {0.0, 0.0, 0.0};
-  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < g.n;
-       row += (int64_t)gridDim.x * blockDim.x) {
-    const int col = (int)(row / g.nz);
-    const int k = (int)(row - (int64_t)col * g.nz);
+  const int n = (int)g.n;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
+    const int col = row / g.nz;
+    const int k = row - col * g.nz;
     bool d = false;
     double asum = 0.0;
     const double ax = row_dot<MASKC, double, double, MODE == 1>(g, val, x, row, col, k, d, &asum);
@@ -333,15 +350,16 @@ __global__ void __launch_bounds__(TPB) k_cg_pupd(int64_t n, const double* __rest
 
 // ---- PCG iteration -----------------------------------------------------------------------------
 
+// 256 threads, at most 64 registers: 4 blocks (32 warps) per SM to hide the gather latency.
 template <int MASKC>
-__global__ void __launch_bounds__(TPB) k_cg_spmv(Geom g, const double* __restrict__ val, const double* __restrict__ p,
-                                                 double* __restrict__ w, double* partials, PcgScalars* sc) {
+__global__ void __launch_bounds__(TPB, 4) k_cg_spmv(Geom g, const double* __restrict__ val, const double* __restrict__ p,
+                                                    double* __restrict__ w, double* partials, PcgScalars* sc) {
   if (sc_done(sc)) return;
   double v[1] = {0.0};
-  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < g.n;
-       row += (int64_t)gridDim.x * blockDim.x) {
-    const int col = (int)(row / g.nz);
-    const int k = (int)(row - (int64_t)col * g.nz);
+  const int n = (int)g.n;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
+    const int col = row / g.nz;
+    const int k = row - col * g.nz;
     bool d = false;
     const double wi = row_dot<MASKC>(g, val, p, row, col, k, d);
     w[row] = wi;
@@ -559,6 +577,117 @@ __global__ void __launch_bounds__(LINE_TPB) k_line_rho(Geom g, const double* __r
   }
 }
 
+// One PCG iteration's update with the vertical-line preconditioner fused in:
+//   x += alpha p, r -= alpha w (rows of LINE_UCOLS whole columns, staged in shared memory),
+//   z = P^{-1} r column by column (one thread per column, in place), then the reductions
+//   (r, r), (r, z) [m'z, 1'r]. The last block tests convergence on (r, r) and forms beta, as
+//   k_cg_update + k_line_rho would; the z of the converged iteration is simply not used.
+constexpr int LINE_UCOLS = 128;
+
+template <int PROJ>
+__global__ void __launch_bounds__(LINE_UCOLS) k_update_line(Geom g, const double* __restrict__ F,
+                                                          double* __restrict__ x, double* __restrict__ r,
+                                                          const double* __restrict__ p, const double* __restrict__ w,
+                                                          double* __restrict__ z, const double* __restrict__ m,
+                                                          double* partials, PcgScalars* sc) {
+  extern __shared__ double smem[];
+  if (sc_done(sc)) return;
+  const double alpha = sc->alpha;
+  const int nz = g.nz, ld = nz + 1;
+  const int ncols = g.ncols;
+  const int n = (int)g.n;
+  const int ntiles = (ncols + LINE_UCOLS - 1) / LINE_UCOLS;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int c0 = tile * LINE_UCOLS;
+    const int cc = min(LINE_UCOLS, ncols - c0);
+    const int row0 = c0 * nz;
+    const int rows = cc * nz;
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+      const int row = row0 + i;
+      x[row] = fma(alpha, p[row], x[row]);
+      const double ri = fma(-alpha, w[row], r[row]);
+      r[row] = ri;
+      smem[(i / nz) * ld + i % nz] = ri;
+      v[0] = fma(ri, ri, v[0]);
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < cc) {
+      const int col = c0 + threadIdx.x;
+      double* col_s = smem + threadIdx.x * ld;
+      double y = 0.0;
+#pragma unroll 4
+      for (int k = 0; k < nz; ++k) {
+        const int li = k * ncols + col;
+        y = (col_s[k] - F[li] * y) * F[n + li];
+        col_s[k] = y;
+      }
+      double zn = y;
+#pragma unroll 4
+      for (int k = nz - 2; k >= 0; --k) {
+        const int li = k * ncols + col;
+        zn = fma(-F[2 * n + li], zn, col_s[k]);
+        col_s[k] = zn;
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+      const int row = row0 + i;
+      const double zi = smem[(i / nz) * ld + i % nz];
+      const double ri = r[row];
+      z[row] = zi;
+      v[1] = fma(ri, zi, v[1]);
+      if (PROJ) {
+        v[2] = fma(m[row], zi, v[2]);
+        v[3] += ri;
+      }
+    }
+    __syncthreads();
+  }
+  if (grid_sum<4>(v, partials, &sc->count[4]) && threadIdx.x == 0) {
+    sc->iter += 1;
+    sc->rr = v[0];
+    if (v[0] <= sc->tol2) {
+      sc->done = 1;
+    } else if (sc->iter >= sc->max_iter) {
+      sc->status = PM_NOT_CONVERGED;
+      sc->done = 1;
+    } else {
+      const double c = PROJ ? v[2] / sc->one_m : 0.0;
+      const double rho_new = v[1] - c * v[3];
+      sc->proj_c = c;
+      sc->beta = rho_new / sc->rho;
+      sc->rho = rho_new;
+      if (!(rho_new > 0.0) || !isfinite(rho_new)) {
+        sc->status = PM_BREAKDOWN;
+        sc->done = 1;
+      }
+    }
+  }
+}
+
+void update_line(pm_operator* op, int which, bool proj, double* x, cudaStream_t s) {
+  SolveCtx* c = op->ctx;
+  Geom g = geom_of(op);
+  const int64_t ntiles = (op->ncols + LINE_UCOLS - 1) / LINE_UCOLS;
+  int grid = (int)std::min<int64_t>(ntiles, std::min<int64_t>((int64_t)op->num_sms * 8, MAX_GRID));
+  if (grid < 1) grid = 1;
+  const size_t smem = (size_t)LINE_UCOLS * (op->nz + 1) * sizeof(double);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_update_line<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_update_line<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  if (proj)
+    k_update_line<1><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line[which], x, c->r, c->p, c->w, c->z, op->d_m,
+                                                    c->partials, c->sc);
+  else
+    k_update_line<0><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line[which], x, c->r, c->p, c->w, c->z, op->d_m,
+                                                    c->partials, c->sc);
+  count_launch();
+}
+
 void line_apply_rho(pm_operator* op, int which, bool proj, int is_first, cudaStream_t s) {
   SolveCtx* c = op->ctx;
   Geom g = geom_of(op);
@@ -684,18 +813,14 @@ void launch_iter(pm_operator* op, int which, const double* val, double* x, bool 
   }
   if (prec == PM_PREC_LINE) {
     {
-      KtScope t(PM_KT_UPDATE, 1, s);
-      k_cg_update<0, 0><<<G, TPB, 0, s>>>(op->n, x, c->r, c->p, c->w, dinv, op->d_m, c->partials, c->sc);
-    }
-    {
       KtScope t(PM_KT_LINE, 1, s);
-      line_apply_rho(op, which, proj, 0, s);
+      update_line(op, which, proj, x, s);
     }
     {
       KtScope t(PM_KT_PUPDATE, 1, s);
       k_cg_pupd<1><<<G, TPB, 0, s>>>(op->n, c->r, dinv, c->z, c->p, c->sc, 0);
     }
-    count_launch(2);
+    count_launch(1);
   } else if (!ic0) {
     {
       KtScope t(PM_KT_UPDATE, 1, s);
@@ -925,6 +1050,629 @@ int pcg_run(pm_operator* op, int which, const double* b, double* x, const pm_sol
   return PM_OK;
 }
 
+// ---- mixed precision: FP32 / BF16 operator values, FP32 inner PCG, FP64 outer refinement -------
+// Outer (FP64): r = b - A x with the FP64 operator; stop when ||r|| <= rtol ||b|| or below the
+// FP64 floor. Inner: PCG on A d = r with the operator values in FP32 (or BF16), FP32 vectors and
+// FP32 SpMV / preconditioner arithmetic, FP64 dot products and alpha / beta, to a relative
+// reduction inner_rtol; then x += d in FP64.
+
+__device__ __forceinline__ float ldv(const float* p, int i) { return __ldg(p + i); }
+__device__ __forceinline__ float ldv(const __nv_bfloat16* p, int i) { return __bfloat162float(p[i]); }
+
+template <int MASKC, typename TV>
+__device__ __forceinline__ float row_dot32(const Geom& g, const TV* __restrict__ val, const float* __restrict__ x,
+                                           int row, int col, int k) {
+  const int nz = g.nz;
+  const int npad = (int)g.npad;
+  int nb[NNBR];
+  uint8_t fl[NNBR];
+  nb[0] = col;
+#pragma unroll
+  for (int q = 1; q < NNBR; ++q) nb[q] = __ldg(g.nbr + col * NNBR + q);
+  if (MASKC >= 0) {
+#pragma unroll
+    for (int q = 0; q < NNBR; ++q) fl[q] = __ldg(g.colflag + (nb[q] >= 0 ? nb[q] : col));
+    if (is_dirichlet(fl[0], k, nz, MASKC)) return x[row];
+  }
+  float a[NSLOT];
+#pragma unroll
+  for (int s = 0; s < NSLOT; ++s) a[s] = ldv(val, s * npad + row);
+  float sum = 0.f;
+#pragma unroll
+  for (int s = 0; s < NSLOT; ++s) {
+    const int q = slot_q(s);
+    const int kk = k + slot_dk(s);
+    bool ok = nb[q] >= 0;
+    if (slot_dk(s) < 0) ok = ok && kk >= 0;
+    if (slot_dk(s) > 0) ok = ok && kk < nz;
+    if (MASKC >= 0) ok = ok && !is_dirichlet(fl[q], kk, nz, MASKC);
+    const float xv = x[ok ? nb[q] * nz + kk : row];
+    sum = fmaf(ok ? a[s] : 0.f, xv, sum);
+  }
+  return sum;
+}
+
+template <int MASKC, typename TV>
+__global__ void __launch_bounds__(TPB, 4) k32_spmv(Geom g, const TV* __restrict__ val, const float* __restrict__ p,
+                                                   float* __restrict__ w, double* partials, PcgScalars* sc) {
+  if (sc_done(sc)) return;
+  double v[1] = {0.0};
+  const int n = (int)g.n;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
+    const int col = row / g.nz;
+    const int k = row - col * g.nz;
+    const float wi = row_dot32<MASKC, TV>(g, val, p, row, col, k);
+    w[row] = wi;
+    v[0] = fma((double)p[row], (double)wi, v[0]);
+  }
+  if (grid_sum<1>(v, partials, &sc->count[3]) && threadIdx.x == 0) {
+    const double pap = v[0];
+    sc->pAp = pap;
+    if (!(pap > 0.0) || !isfinite(pap)) {
+      sc->status = PM_BREAKDOWN;
+      sc->done = 1;
+    } else {
+      sc->alpha = sc->rho / pap;
+    }
+  }
+}
+
+// d += alpha p, r -= alpha w; INLINE_Z: z = dinv r (Jacobi) and its reductions.
+template <int PROJ, int INLINE_Z>
+__global__ void __launch_bounds__(TPB) k32_update(int64_t n, float* __restrict__ d, float* __restrict__ r,
+                                                  const float* __restrict__ p, const float* __restrict__ w,
+                                                  const float* __restrict__ dinv, const double* __restrict__ m,
+                                                  double* partials, PcgScalars* sc) {
+  if (sc_done(sc)) return;
+  const float alpha = (float)sc->alpha;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    d[i] = fmaf(alpha, p[i], d[i]);
+    const float ri = fmaf(-alpha, w[i], r[i]);
+    r[i] = ri;
+    v[0] = fma((double)ri, (double)ri, v[0]);
+    if (INLINE_Z) {
+      const float zi = dinv[i] * ri;
+      v[1] = fma((double)ri, (double)zi, v[1]);
+      if (PROJ) {
+        v[2] = fma(m[i], (double)zi, v[2]);
+        v[3] += (double)ri;
+      }
+    }
+  }
+  if (grid_sum<4>(v, partials, &sc->count[4]) && threadIdx.x == 0) {
+    sc->iter += 1;
+    sc->rr = v[0];
+    if (v[0] <= sc->tol2) {
+      sc->done = 1;
+    } else if (sc->iter >= sc->max_iter) {
+      sc->status = PM_NOT_CONVERGED;
+      sc->done = 1;
+    } else if (INLINE_Z) {
+      const double c = PROJ ? v[2] / sc->one_m : 0.0;
+      const double rho_new = v[1] - c * v[3];
+      sc->proj_c = c;
+      sc->beta = rho_new / sc->rho;
+      sc->rho = rho_new;
+      if (!(rho_new > 0.0) || !isfinite(rho_new)) {
+        sc->status = PM_BREAKDOWN;
+        sc->done = 1;
+      }
+    }
+  }
+}
+
+// rho = (r, z') with z' = z - c (pressure) from stored or inline z; first: beta = 0.
+template <int PROJ, int STORED>
+__global__ void __launch_bounds__(TPB) k32_rho(int64_t n, const float* __restrict__ r, const float* __restrict__ dinv,
+                                               const float* __restrict__ zbuf, const double* __restrict__ m,
+                                               double* partials, PcgScalars* sc, int is_first) {
+  if (!is_first && sc_done(sc)) return;
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float ri = r[i];
+    const float zi = STORED ? zbuf[i] : dinv[i] * ri;
+    v[0] = fma((double)ri, (double)zi, v[0]);
+    if (PROJ) {
+      v[1] = fma(m[i], (double)zi, v[1]);
+      v[2] += (double)ri;
+    }
+  }
+  if (grid_sum<3>(v, partials, &sc->count[2]) && threadIdx.x == 0) {
+    const double c = PROJ ? v[1] / sc->one_m : 0.0;
+    const double rho_new = v[0] - c * v[2];
+    sc->proj_c = c;
+    if (is_first) {
+      sc->rho = rho_new;
+      sc->beta = 0.0;
+    } else {
+      sc->beta = rho_new / sc->rho;
+      sc->rho = rho_new;
+    }
+    if ((!(rho_new > 0.0) || !isfinite(rho_new)) && !sc->done) {
+      sc->status = PM_BREAKDOWN;
+      sc->done = 1;
+    }
+  }
+}
+
+template <int STORED>
+__global__ void __launch_bounds__(TPB) k32_pupd(int64_t n, const float* __restrict__ r, const float* __restrict__ dinv,
+                                                const float* __restrict__ zbuf, float* __restrict__ p,
+                                                const PcgScalars* sc, int is_first) {
+  if (!is_first && sc_done(sc)) return;
+  const float beta = (float)sc->beta, c = (float)sc->proj_c;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float zi = (STORED ? zbuf[i] : dinv[i] * r[i]) - c;
+    p[i] = is_first ? zi : fmaf(beta, p[i], zi);
+  }
+}
+
+// Inner start: r32 = (float) r64, d32 = 0, grid (r, r) in FP64 -> inner tolerance.
+__global__ void __launch_bounds__(TPB) k32_start(int64_t n, const double* __restrict__ r64, float* __restrict__ r32,
+                                                 float* __restrict__ d32, double inner_rtol, double* partials,
+                                                 PcgScalars* sc) {
+  double v[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float ri = (float)r64[i];
+    r32[i] = ri;
+    d32[i] = 0.f;
+    v[0] = fma((double)ri, (double)ri, v[0]);
+  }
+  if (grid_sum<1>(v, partials, &sc->count[1]) && threadIdx.x == 0) {
+    sc->bb = v[0];
+    sc->rr = v[0];
+    sc->tol2 = inner_rtol * inner_rtol * v[0];
+    sc->done = v[0] == 0.0 ? 1 : 0;
+  }
+}
+
+__global__ void k_fill32(float* x, int64_t n, float v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) x[i] = v;
+}
+
+__global__ void k_add_f32(int64_t n, double* __restrict__ x, const float* __restrict__ d) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += (double)d[i];
+}
+
+template <typename T>
+__global__ void k_cvt(int64_t n, const double* __restrict__ in, T* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if constexpr (std::is_same<T, float>::value) out[i] = (float)in[i];
+    else out[i] = __double2bfloat16(in[i]);
+  }
+}
+
+// FP32 vertical-line solve fused with the inner update (as k_update_line).
+template <int PROJ>
+__global__ void __launch_bounds__(LINE_UCOLS) k32_update_line(Geom g, const float* __restrict__ F,
+                                                            float* __restrict__ d, float* __restrict__ r,
+                                                            const float* __restrict__ p, const float* __restrict__ w,
+                                                            float* __restrict__ z, const double* __restrict__ m,
+                                                            double* partials, PcgScalars* sc, int update) {
+  extern __shared__ float smf[];
+  if (update && sc_done(sc)) return;
+  const float alpha = update ? (float)sc->alpha : 0.f;
+  const int nz = g.nz, ld = nz + 1;
+  const int ncols = g.ncols;
+  const int n = (int)g.n;
+  const int ntiles = (ncols + LINE_UCOLS - 1) / LINE_UCOLS;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int c0 = tile * LINE_UCOLS;
+    const int cc = min(LINE_UCOLS, ncols - c0);
+    const int row0 = c0 * nz;
+    const int rows = cc * nz;
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+      const int row = row0 + i;
+      float ri = r[row];
+      if (update) {
+        d[row] = fmaf(alpha, p[row], d[row]);
+        ri = fmaf(-alpha, w[row], ri);
+        r[row] = ri;
+      }
+      smf[(i / nz) * ld + i % nz] = ri;
+      v[0] = fma((double)ri, (double)ri, v[0]);
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < cc) {
+      const int col = c0 + threadIdx.x;
+      float* col_s = smf + threadIdx.x * ld;
+      float y = 0.f;
+#pragma unroll 4
+      for (int k = 0; k < nz; ++k) {
+        const int li = k * ncols + col;
+        y = (col_s[k] - F[li] * y) * F[n + li];
+        col_s[k] = y;
+      }
+      float zn = y;
+#pragma unroll 4
+      for (int k = nz - 2; k >= 0; --k) {
+        const int li = k * ncols + col;
+        zn = fmaf(-F[2 * n + li], zn, col_s[k]);
+        col_s[k] = zn;
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+      const int row = row0 + i;
+      const float zi = smf[(i / nz) * ld + i % nz];
+      const float ri = r[row];
+      z[row] = zi;
+      v[1] = fma((double)ri, (double)zi, v[1]);
+      if (PROJ) {
+        v[2] = fma(m[row], (double)zi, v[2]);
+        v[3] += (double)ri;
+      }
+    }
+    __syncthreads();
+  }
+  if (grid_sum<4>(v, partials, &sc->count[4]) && threadIdx.x == 0) {
+    const double c = PROJ ? v[2] / sc->one_m : 0.0;
+    const double rho_new = v[1] - c * v[3];
+    if (!update) {
+      sc->proj_c = c;
+      sc->rho = rho_new;
+      sc->beta = 0.0;
+      if ((!(rho_new > 0.0) || !isfinite(rho_new)) && !sc->done) {
+        sc->status = PM_BREAKDOWN;
+        sc->done = 1;
+      }
+    } else {
+      sc->iter += 1;
+      sc->rr = v[0];
+      if (v[0] <= sc->tol2) {
+        sc->done = 1;
+      } else if (sc->iter >= sc->max_iter) {
+        sc->status = PM_NOT_CONVERGED;
+        sc->done = 1;
+      } else {
+        sc->proj_c = c;
+        sc->beta = rho_new / sc->rho;
+        sc->rho = rho_new;
+        if (!(rho_new > 0.0) || !isfinite(rho_new)) {
+          sc->status = PM_BREAKDOWN;
+          sc->done = 1;
+        }
+      }
+    }
+  }
+}
+
+// FP32 IC0 colour sweep (as k_ic0_sweep).
+template <int COLOUR, int FWD>
+__global__ void __launch_bounds__(TPB) k32_ic0_sweep(Geom g, CMap cm, const int32_t* __restrict__ cls_cols,
+                                                     int64_t cls_off, int64_t cls_cnt, const float* __restrict__ F,
+                                                     const float* __restrict__ r, float* __restrict__ y,
+                                                     const PcgScalars* sc, int check_done) {
+  if (check_done && sc_done(sc)) return;
+  constexpr int kpar = COLOUR >> 2;
+  const int nlev = cm.nlev[kpar];
+  const int64_t total = cls_cnt * nlev;
+  const int nz = g.nz;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int col = __ldg(cls_cols + cls_off + t / nlev);
+    const int k = 2 * (int)(t % nlev) + kpar;
+    const int64_t row = (int64_t)col * nz + k;
+    const int64_t pi = cm.cbase[COLOUR] + t;
+    float acc = FWD ? r[row] : y[row];
+#pragma unroll
+    for (int s = 0; s < NSLOT; ++s) {
+      if (s == DIAG_SLOT) continue;
+      const int cj = COLOUR ^ slot_flip(s);
+      if (FWD ? (cj > COLOUR) : (cj < COLOUR)) continue;
+      const int q = slot_q(s);
+      const int kk = k + slot_dk(s);
+      if (kk < 0 || kk >= nz) continue;
+      const int nb = q == 0 ? col : __ldg(g.nbr + (int64_t)col * NNBR + q);
+      if (nb < 0) continue;
+      acc = fmaf(-F[(int64_t)s * g.n + pi], y[(int64_t)nb * nz + kk], acc);
+    }
+    y[row] = acc / F[(int64_t)DIAG_SLOT * g.n + pi];
+  }
+}
+
+void ic0_apply32(pm_operator* op, int which, const float* r, float* z, const PcgScalars* sc, int check_done,
+                 cudaStream_t s) {
+  Geom g = geom_of(op);
+  CMap cm = cmap_of(op);
+  const float* F = op->d_ic0_32[which];
+  int64_t off[5] = {0, 0, 0, 0, 0};
+  for (int c = 0; c < 4; ++c) off[c + 1] = off[c] + op->cls_count[c];
+#define PM_SWEEP32(C, FW)                                                                      \
+  {                                                                                            \
+    const int64_t cnt = op->cls_count[(C) & 3];                                                \
+    const int64_t tot = cnt * cm.nlev[(C) >> 2];                                               \
+    if (tot > 0) {                                                                             \
+      k32_ic0_sweep<C, FW><<<grid_for(tot, TPB, op->num_sms), TPB, 0, s>>>(                    \
+          g, cm, op->d_cls_cols, off[(C) & 3], cnt, F, r, z, sc, check_done);                  \
+      count_launch();                                                                          \
+    }                                                                                          \
+  }
+  PM_SWEEP32(0, 1) PM_SWEEP32(1, 1) PM_SWEEP32(2, 1) PM_SWEEP32(3, 1)
+  PM_SWEEP32(4, 1) PM_SWEEP32(5, 1) PM_SWEEP32(6, 1) PM_SWEEP32(7, 1)
+  PM_SWEEP32(7, 0) PM_SWEEP32(6, 0) PM_SWEEP32(5, 0) PM_SWEEP32(4, 0)
+  PM_SWEEP32(3, 0) PM_SWEEP32(2, 0) PM_SWEEP32(1, 0) PM_SWEEP32(0, 0)
+#undef PM_SWEEP32
+}
+
+int ensure_mixed(pm_operator* op, int which, int precision, int prec, cudaStream_t s) {
+  SolveCtx* c = op->ctx;
+  const size_t fb = (size_t)op->n * sizeof(float);
+  if (!c->r32) {
+    cudaError_t e = cudaSuccess;
+    e = e ? e : cudaMalloc((void**)&c->r32, fb);
+    e = e ? e : cudaMalloc((void**)&c->p32, fb);
+    e = e ? e : cudaMalloc((void**)&c->w32, fb);
+    e = e ? e : cudaMalloc((void**)&c->z32, fb);
+    e = e ? e : cudaMalloc((void**)&c->d32, fb);
+    e = e ? e : cudaMalloc((void**)&c->sc_in, sizeof(PcgScalars));
+    e = e ? e : cudaMallocHost((void**)&c->sc_in_host, sizeof(PcgScalars));
+    if (e != cudaSuccess) return cuda_check(e, "mixed-precision workspace");
+    op->device_bytes += 5 * (int64_t)fb;
+  }
+  const int vs = which_valset(which);
+  const int64_t nv = (int64_t)NSLOT * op->npad;
+  const int G = grid_for(nv, TPB, op->num_sms);
+  if (precision == PM_FP32_REFINE && !op->d_val32[vs]) {
+    int st = cuda_check(cudaMalloc((void**)&op->d_val32[vs], nv * sizeof(float)), "cudaMalloc fp32 values");
+    if (st) return st;
+    op->device_bytes += nv * 4;
+    k_cvt<float><<<G, TPB, 0, s>>>(nv, op->d_val[vs], op->d_val32[vs]);
+    count_launch();
+  }
+  if (precision == PM_BF16_REFINE && !op->d_val16[vs]) {
+    int st = cuda_check(cudaMalloc((void**)&op->d_val16[vs], nv * sizeof(uint16_t)), "cudaMalloc bf16 values");
+    if (st) return st;
+    op->device_bytes += nv * 2;
+    k_cvt<__nv_bfloat16><<<G, TPB, 0, s>>>(nv, op->d_val[vs], reinterpret_cast<__nv_bfloat16*>(op->d_val16[vs]));
+    count_launch();
+  }
+  if (prec == PM_PREC_LINE && !op->d_line32[which]) {
+    int st = cuda_check(cudaMalloc((void**)&op->d_line32[which], 3 * fb), "cudaMalloc fp32 line");
+    if (st) return st;
+    op->device_bytes += 3 * (int64_t)fb;
+    k_cvt<float><<<grid_for(3 * op->n, TPB, op->num_sms), TPB, 0, s>>>(3 * op->n, op->d_line[which], op->d_line32[which]);
+    count_launch();
+  }
+  if (prec == PM_PREC_IC0 && !op->d_ic0_32[which]) {
+    int st = cuda_check(cudaMalloc((void**)&op->d_ic0_32[which], (size_t)NSLOT * fb), "cudaMalloc fp32 ic0");
+    if (st) return st;
+    op->device_bytes += (int64_t)NSLOT * fb;
+    k_cvt<float><<<grid_for(NSLOT * op->n, TPB, op->num_sms), TPB, 0, s>>>(NSLOT * op->n, op->ic0[which].F,
+                                                                          op->d_ic0_32[which]);
+    count_launch();
+  }
+  return cuda_check(cudaGetLastError(), "mixed set-up");
+}
+
+int read_inner(SolveCtx* c, cudaStream_t s) {
+  int st = cuda_check(cudaMemcpyAsync(c->sc_in_host, c->sc_in, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s), "scalars");
+  if (st) return st;
+  st = cuda_check(cudaStreamSynchronize(s), "mixed pcg sync");
+  if (!st && !g_kt.pending.empty()) kt_collect();
+  return st;
+}
+
+// Algorithmic bytes per inner iteration per row (values at vbytes each).
+double bytes_per_inner(const pm_operator* op, int prec, int vbytes) {
+  const double n = (double)op->n;
+  double b = n * (15 * vbytes + 4 + 4);                       // SpMV: values, p, w
+  if (prec == PM_PREC_LINE) b += n * (16 + 8 + 12 + 4 + 4 + 12);  // fused update + line, p-update
+  else if (prec == PM_PREC_IC0) b += n * (24 + 2 * 8 * 4 + 4 * 4 + 8 + 12);
+  else b += n * (20 + 8 + 16);                                 // Jacobi update, p-update
+  return b;
+}
+
+template <int MASKC, typename TV>
+void inner_iter(pm_operator* op, int which, const TV* val32, bool proj, int prec, const float* dinv32, cudaStream_t s) {
+  SolveCtx* c = op->ctx;
+  Geom g = geom_of(op);
+  const int G = grid_for(op->n, TPB, op->num_sms);
+  {
+    KtScope t(PM_KT_SPMV, 1, s);
+    k32_spmv<MASKC, TV><<<G, TPB, 0, s>>>(g, val32, c->p32, c->w32, c->partials, c->sc_in);
+  }
+  if (prec == PM_PREC_LINE) {
+    const int64_t ntiles = (op->ncols + LINE_UCOLS - 1) / LINE_UCOLS;
+    int grid = (int)std::min<int64_t>(ntiles, std::min<int64_t>((int64_t)op->num_sms * 8, MAX_GRID));
+    const size_t smem = (size_t)LINE_UCOLS * (op->nz + 1) * sizeof(float);
+    {
+      KtScope t(PM_KT_LINE, 1, s);
+      if (proj)
+        k32_update_line<1><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], c->d32, c->r32, c->p32, c->w32,
+                                                          c->z32, op->d_m, c->partials, c->sc_in, 1);
+      else
+        k32_update_line<0><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], c->d32, c->r32, c->p32, c->w32,
+                                                          c->z32, op->d_m, c->partials, c->sc_in, 1);
+    }
+    {
+      KtScope t(PM_KT_PUPDATE, 1, s);
+      k32_pupd<1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, c->p32, c->sc_in, 0);
+    }
+    count_launch(3);
+  } else if (prec == PM_PREC_IC0) {
+    {
+      KtScope t(PM_KT_UPDATE, 1, s);
+      k32_update<0, 0><<<G, TPB, 0, s>>>(op->n, c->d32, c->r32, c->p32, c->w32, dinv32, op->d_m, c->partials, c->sc_in);
+    }
+    {
+      KtScope t(PM_KT_IC0, 16, s);
+      ic0_apply32(op, which, c->r32, c->z32, c->sc_in, 1, s);
+    }
+    {
+      KtScope t(PM_KT_PUPDATE, 2, s);
+      if (proj) k32_rho<1, 1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, op->d_m, c->partials, c->sc_in, 0);
+      else k32_rho<0, 1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, op->d_m, c->partials, c->sc_in, 0);
+      k32_pupd<1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, c->p32, c->sc_in, 0);
+    }
+    count_launch(4);
+  } else {
+    {
+      KtScope t(PM_KT_UPDATE, 1, s);
+      if (proj) k32_update<1, 1><<<G, TPB, 0, s>>>(op->n, c->d32, c->r32, c->p32, c->w32, dinv32, op->d_m, c->partials, c->sc_in);
+      else k32_update<0, 1><<<G, TPB, 0, s>>>(op->n, c->d32, c->r32, c->p32, c->w32, dinv32, op->d_m, c->partials, c->sc_in);
+    }
+    {
+      KtScope t(PM_KT_PUPDATE, 1, s);
+      k32_pupd<0><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, nullptr, c->p32, c->sc_in, 0);
+    }
+    count_launch(3);
+  }
+}
+
+void inner_first(pm_operator* op, int which, bool proj, int prec, const float* dinv32, cudaStream_t s) {
+  SolveCtx* c = op->ctx;
+  Geom g = geom_of(op);
+  const int G = grid_for(op->n, TPB, op->num_sms);
+  if (prec == PM_PREC_LINE) {
+    const int64_t ntiles = (op->ncols + LINE_UCOLS - 1) / LINE_UCOLS;
+    int grid = (int)std::min<int64_t>(ntiles, std::min<int64_t>((int64_t)op->num_sms * 8, MAX_GRID));
+    const size_t smem = (size_t)LINE_UCOLS * (op->nz + 1) * sizeof(float);
+    if (proj)
+      k32_update_line<1><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], c->d32, c->r32, c->p32, c->w32,
+                                                        c->z32, op->d_m, c->partials, c->sc_in, 0);
+    else
+      k32_update_line<0><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], c->d32, c->r32, c->p32, c->w32,
+                                                        c->z32, op->d_m, c->partials, c->sc_in, 0);
+    k32_pupd<1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, c->p32, c->sc_in, 1);
+  } else if (prec == PM_PREC_IC0) {
+    ic0_apply32(op, which, c->r32, c->z32, c->sc_in, 0, s);
+    if (proj) k32_rho<1, 1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, op->d_m, c->partials, c->sc_in, 1);
+    else k32_rho<0, 1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, op->d_m, c->partials, c->sc_in, 1);
+    k32_pupd<1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, c->p32, c->sc_in, 1);
+  } else {
+    if (proj) k32_rho<1, 0><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, nullptr, op->d_m, c->partials, c->sc_in, 1);
+    else k32_rho<0, 0><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, nullptr, op->d_m, c->partials, c->sc_in, 1);
+    k32_pupd<0><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, nullptr, c->p32, c->sc_in, 1);
+  }
+  count_launch(2);
+}
+
+template <int MASKC, typename TV>
+int mixed_run(pm_operator* op, int which, const double* b, double* x, const pm_solve_opts* o, pm_solve_stats* stats,
+              cudaStream_t s) {
+  auto t0 = std::chrono::steady_clock::now();
+  SolveCtx* c = op->ctx;
+  const bool proj = which == PM_OP_PRESSURE;
+  const int prec = o->prec;
+  const double* val64 = op->d_val[which_valset(which)];
+  int st;
+  if ((st = launch_dinv(op, which, s))) return st;
+  if (prec == PM_PREC_IC0 && !op->ic0[which].ok) {
+    int bd = 0;
+    for (int m = -1; m <= 10; ++m) {
+      if ((st = launch_ic0_factor(op, which, m < 0 ? 0.0 : 1e-3 * std::pow(2.0, m), &bd, s))) return st;
+      if (!bd) break;
+    }
+    if (bd) return set_error(PM_BREAKDOWN, "IC0 pivot failure after the shift limit");
+  }
+  if (prec == PM_PREC_LINE && (st = line_factor(op, which, s))) return st;
+  if ((st = ensure_mixed(op, which, o->precision, prec, s))) return st;
+  const int vs = which_valset(which);
+  const TV* val32 = std::is_same<TV, float>::value ? reinterpret_cast<const TV*>(op->d_val32[vs])
+                                                   : reinterpret_cast<const TV*>(op->d_val16[vs]);
+  const float* dinv32 = op->d_dinv32[which];
+  if (prec == PM_PREC_NONE) {  // plain CG: z = r, held as an all-ones diagonal in z32
+    k_fill32<<<grid_for(op->n, TPB, op->num_sms), TPB, 0, s>>>(c->z32, op->n, 1.f);
+    count_launch();
+    dinv32 = c->z32;
+  }
+  const double inner_rtol = o->inner_rtol > 0.0 ? o->inner_rtol
+                                                : (std::is_same<TV, float>::value ? 1e-4 : 1e-2);
+  const int G = grid_for(op->n, TPB, op->num_sms);
+  PcgScalars init;
+  std::memset(&init, 0, sizeof(init));
+  init.one_m = op->one_m;
+  init.max_iter = o->max_iter;
+  if ((st = cuda_check(cudaMemcpyAsync(c->sc, &init, sizeof(init), cudaMemcpyHostToDevice, s), "scalars init"))) return st;
+  const double* bw = b;
+  if (proj) {
+    k_cg_press_sums<<<G, TPB, 0, s>>>(op->n, b, x, op->d_m, o->x0_is_guess ? 1 : 0, c->partials, c->sc);
+    k_cg_prepare<<<G, TPB, 0, s>>>(op->n, b, op->d_m, c->bw, x, 1, o->x0_is_guess ? 1 : 0, c->sc);
+    count_launch(2);
+    bw = c->bw;
+  } else if (!o->x0_is_guess) {
+    k_cg_prepare<<<G, TPB, 0, s>>>(op->n, b, op->d_m, nullptr, x, 0, 0, c->sc);
+    count_launch();
+  }
+  launch_residual<MASKC>(op, val64, bw, x, o->rtol, 0, s);
+  if ((st = read_scalars(c, s))) return st;
+  const double bb = c->sc_host->bb;
+  int outer = 0, inner_total = 0, status = PM_OK;
+  double rel_true = 0.0, rel_floor = 0.0, bytes = 0.0;
+  const int vbytes = std::is_same<TV, float>::value ? 4 : 2;
+  if (c->sc_host->zero_rhs) {
+    k_fill<<<G, TPB, 0, s>>>(x, op->n, 0.0);
+    count_launch();
+  } else {
+    for (;;) {
+      launch_residual<MASKC>(op, val64, bw, x, o->rtol, 1, s);   // FP64 true residual into c->r
+      if ((st = read_scalars(c, s))) return st;
+      rel_true = std::sqrt(c->sc_host->aux[0] / bb);
+      rel_floor = std::ldexp(1.0, -53) * std::sqrt(c->sc_host->aux[1] / bb);
+      bytes += (double)op->n * (15 * 8 + 3 * 8);
+      if (rel_true <= std::max(o->rtol, rel_floor)) break;
+      if (inner_total >= o->max_iter || outer >= 64) {
+        status = PM_NOT_CONVERGED;
+        break;
+      }
+      // inner solve A32 d = r in FP32
+      PcgScalars in;
+      std::memset(&in, 0, sizeof(in));
+      in.one_m = op->one_m;
+      in.max_iter = o->max_iter - inner_total;
+      if ((st = cuda_check(cudaMemcpyAsync(c->sc_in, &in, sizeof(in), cudaMemcpyHostToDevice, s), "scalars"))) return st;
+      k32_start<<<G, TPB, 0, s>>>(op->n, c->r, c->r32, c->d32, inner_rtol, c->partials, c->sc_in);
+      count_launch();
+      inner_first(op, which, proj, prec, dinv32, s);
+      if ((st = read_inner(c, s))) return st;
+      int64_t issued = 0;
+      int chunk = 4;
+      while (!c->sc_in_host->done) {
+        if (issued > (int64_t)in.max_iter + 4096) return set_error(PM_ECUDA, "mixed PCG: device never reported completion");
+        for (int it = 0; it < chunk; ++it) inner_iter<MASKC, TV>(op, which, val32, proj, prec, dinv32, s);
+        issued += chunk;
+        if ((st = read_inner(c, s))) return st;
+        if (chunk < 64) chunk *= 2;
+      }
+      const int its = c->sc_in_host->iter;
+      inner_total += its;
+      bytes += its * bytes_per_inner(op, prec, vbytes);
+      if (c->sc_in_host->status == PM_BREAKDOWN && its == 0) {
+        status = PM_BREAKDOWN;
+        break;
+      }
+      k_add_f32<<<G, TPB, 0, s>>>(op->n, x, c->d32);
+      count_launch();
+      ++outer;
+    }
+  }
+  if (proj) {
+    k_cg_press_sums<<<G, TPB, 0, s>>>(op->n, b, x, op->d_m, 1, c->partials, c->sc);
+    k_shift_by<<<G, TPB, 0, s>>>(x, op->n, c->sc);
+    count_launch(2);
+    if ((st = read_scalars(c, s))) return st;
+  }
+  if (stats) {
+    stats->iters = inner_total;
+    stats->outer_iters = outer;
+    stats->first_pass_iters = inner_total;
+    stats->status = status;
+    stats->rel_residual_true = c->sc_host->zero_rhs ? 0.0 : rel_true;
+    stats->rel_residual_rec = stats->rel_residual_true;
+    stats->rel_residual_floor = rel_floor;
+    stats->bytes_moved = bytes;
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if ((st = cuda_check(cudaGetLastError(), "mixed pcg kernels"))) return st;
+  if (status != PM_OK)
+    return set_error(status, status == PM_NOT_CONVERGED ? "mixed-precision PCG did not reach rtol"
+                                                        : "mixed-precision PCG breakdown");
+  return PM_OK;
+}
+
 }  // namespace
 
 int spmv(pm_operator* op, int which, const double* x, double* y, cudaStream_t s) {
@@ -947,8 +1695,25 @@ int pcg_solve(pm_operator* op, int which, const double* b, double* x, const pm_s
   if (!which_symmetric(which)) return set_error(PM_EINVAL, "pcg needs a symmetric operator");
   if (o->prec < 0 || o->prec > PM_PREC_LINE) return set_error(PM_EINVAL, "unknown preconditioner");
   if (!(o->rtol > 0.0) || o->max_iter < 0) return set_error(PM_EINVAL, "rtol must be > 0, max_iter >= 0");
+  if (o->precision < PM_FP64 || o->precision > PM_BF16_REFINE) return set_error(PM_EINVAL, "unknown precision");
   int r = ensure_ctx(op);
   if (r) return r;
+  if (o->precision == PM_FP32_REFINE) {
+    switch (which_mask(which)) {
+      case 0: return mixed_run<0, float>(op, which, b, x, o, st, s);
+      case 1: return mixed_run<1, float>(op, which, b, x, o, st, s);
+      case 2: return mixed_run<2, float>(op, which, b, x, o, st, s);
+      default: return mixed_run<-1, float>(op, which, b, x, o, st, s);
+    }
+  }
+  if (o->precision == PM_BF16_REFINE) {
+    switch (which_mask(which)) {
+      case 0: return mixed_run<0, __nv_bfloat16>(op, which, b, x, o, st, s);
+      case 1: return mixed_run<1, __nv_bfloat16>(op, which, b, x, o, st, s);
+      case 2: return mixed_run<2, __nv_bfloat16>(op, which, b, x, o, st, s);
+      default: return mixed_run<-1, __nv_bfloat16>(op, which, b, x, o, st, s);
+    }
+  }
   switch (which_mask(which)) {
     case 0: return pcg_run<0>(op, which, b, x, o, st, s);
     case 1: return pcg_run<1>(op, which, b, x, o, st, s);
@@ -998,6 +1763,13 @@ void destroy_ctx(pm_operator* op) {
   cudaFree(c->partials);
   cudaFree(c->sc);
   cudaFreeHost(c->sc_host);
+  cudaFree(c->r32);
+  cudaFree(c->p32);
+  cudaFree(c->w32);
+  cudaFree(c->z32);
+  cudaFree(c->d32);
+  cudaFree(c->sc_in);
+  if (c->sc_in_host) cudaFreeHost(c->sc_in_host);
   delete c;
   op->ctx = nullptr;
 }
