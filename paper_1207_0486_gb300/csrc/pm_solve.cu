@@ -408,6 +408,8 @@ __global__ void __launch_bounds__(TPB) k_cg_update(int64_t n, double* __restrict
     } else if (sc->iter >= sc->max_iter) {
       sc->status = PM_NOT_CONVERGED;
       sc->done = 1;
+    } else if (v[0] <= sc->aux[2]) {
+      sc->done = 2;  // residual replacement requested (mixed precision): the host finishes the step
     } else if (INLINE_Z) {
       const double c = PROJ ? v[2] / sc->one_m : 0.0;
       const double rho_new = v[1] - c * v[3];
@@ -1059,6 +1061,14 @@ int pcg_run(pm_operator* op, int which, const double* b, double* x, const pm_sol
 __device__ __forceinline__ float ldv(const float* p, int i) { return __ldg(p + i); }
 __device__ __forceinline__ float ldv(const __nv_bfloat16* p, int i) { return __bfloat162float(p[i]); }
 
+// Low-precision operator in difference form. The low-precision copy keeps the 14 off-diagonal
+// values and stores, in the diagonal slot, the FP64 row sum rs_i = sum_j a_ij (0 for the pure-
+// Neumann pressure operator). Then
+//   (A x)_i = (rs_i - sum_{j eliminated} a_ij) x_i + sum_{j kept, j != i} a_ij (x_j - x_i),
+// which is A x exactly, but rounds each a_ij (x_j - x_i) instead of cancelling large a_ij x_j
+// terms: for vectors that are smooth along the strong (vertical) couplings this keeps the
+// relative accuracy that FP32 / BF16 would otherwise lose on the thin-domain operators, and the
+// constant null space of the pressure operator is exact in any precision.
 template <int MASKC, typename TV>
 __device__ __forceinline__ float row_dot32(const Geom& g, const TV* __restrict__ val, const float* __restrict__ x,
                                            int row, int col, int k) {
@@ -1077,19 +1087,48 @@ __device__ __forceinline__ float row_dot32(const Geom& g, const TV* __restrict__
   float a[NSLOT];
 #pragma unroll
   for (int s = 0; s < NSLOT; ++s) a[s] = ldv(val, s * npad + row);
-  float sum = 0.f;
+  const float xi = x[row];
+  float sum = 0.f, drop = 0.f;
 #pragma unroll
   for (int s = 0; s < NSLOT; ++s) {
+    if (s == DIAG_SLOT) continue;
     const int q = slot_q(s);
     const int kk = k + slot_dk(s);
     bool ok = nb[q] >= 0;
     if (slot_dk(s) < 0) ok = ok && kk >= 0;
     if (slot_dk(s) > 0) ok = ok && kk < nz;
-    if (MASKC >= 0) ok = ok && !is_dirichlet(fl[q], kk, nz, MASKC);
-    const float xv = x[ok ? nb[q] * nz + kk : row];
-    sum = fmaf(ok ? a[s] : 0.f, xv, sum);
+    bool keep = ok;
+    if (MASKC >= 0) {
+      const bool dj = ok && is_dirichlet(fl[q], kk, nz, MASKC);
+      keep = ok && !dj;
+      drop += dj ? a[s] : 0.f;
+    }
+    const float xv = x[keep ? nb[q] * nz + kk : row];
+    sum = fmaf(keep ? a[s] : 0.f, xv - xi, sum);
   }
-  return sum;
+  return fmaf(a[DIAG_SLOT] - drop, xi, sum);
+}
+
+// Low-precision copy in difference form: off-diagonals rounded, diagonal slot = FP64 row sum
+// (zero_rowsum: exactly 0, the pure-Neumann operator).
+template <typename T>
+__global__ void k_cvt_diff(int64_t n, int64_t npad, const double* __restrict__ val, T* __restrict__ out,
+                           int zero_rowsum) {
+  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < npad; row += (int64_t)gridDim.x * blockDim.x) {
+    double rs = 0.0;
+#pragma unroll
+    for (int s = 0; s < NSLOT; ++s) {
+      const double v = val[s * npad + row];
+      rs += v;
+      if (s != DIAG_SLOT) {
+        if constexpr (std::is_same<T, float>::value) out[s * npad + row] = (float)v;
+        else out[s * npad + row] = __double2bfloat16(v);
+      }
+    }
+    if (zero_rowsum || row >= n) rs = 0.0;
+    if constexpr (std::is_same<T, float>::value) out[DIAG_SLOT * npad + row] = (float)rs;
+    else out[DIAG_SLOT * npad + row] = __double2bfloat16(rs);
+  }
 }
 
 template <int MASKC, typename TV>
@@ -1117,17 +1156,18 @@ __global__ void __launch_bounds__(TPB, 4) k32_spmv(Geom g, const TV* __restrict_
   }
 }
 
-// d += alpha p, r -= alpha w; INLINE_Z: z = dinv r (Jacobi) and its reductions.
+// x += alpha p (x in FP64), r -= alpha w (FP32); INLINE_Z: z = dinv r (Jacobi) and its reductions.
 template <int PROJ, int INLINE_Z>
-__global__ void __launch_bounds__(TPB) k32_update(int64_t n, float* __restrict__ d, float* __restrict__ r,
+__global__ void __launch_bounds__(TPB) k32_update(int64_t n, double* __restrict__ x, float* __restrict__ r,
                                                   const float* __restrict__ p, const float* __restrict__ w,
                                                   const float* __restrict__ dinv, const double* __restrict__ m,
                                                   double* partials, PcgScalars* sc) {
   if (sc_done(sc)) return;
-  const float alpha = (float)sc->alpha;
+  const double alpha_d = sc->alpha;
+  const float alpha = (float)alpha_d;
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    d[i] = fmaf(alpha, p[i], d[i]);
+    x[i] = fma(alpha_d, (double)p[i], x[i]);
     const float ri = fmaf(-alpha, w[i], r[i]);
     r[i] = ri;
     v[0] = fma((double)ri, (double)ri, v[0]);
@@ -1148,6 +1188,8 @@ __global__ void __launch_bounds__(TPB) k32_update(int64_t n, float* __restrict__
     } else if (sc->iter >= sc->max_iter) {
       sc->status = PM_NOT_CONVERGED;
       sc->done = 1;
+    } else if (v[0] <= sc->aux[2]) {
+      sc->done = 2;  // residual replacement requested (mixed precision): the host finishes the step
     } else if (INLINE_Z) {
       const double c = PROJ ? v[2] / sc->one_m : 0.0;
       const double rho_new = v[1] - c * v[3];
@@ -1227,6 +1269,11 @@ __global__ void __launch_bounds__(TPB) k32_start(int64_t n, const double* __rest
   }
 }
 
+__global__ void k32_from64(int64_t n, const double* __restrict__ r64, float* __restrict__ r32) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    r32[i] = (float)r64[i];
+}
+
 __global__ void k_fill32(float* x, int64_t n, float v) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) x[i] = v;
 }
@@ -1247,13 +1294,17 @@ __global__ void k_cvt(int64_t n, const double* __restrict__ in, T* __restrict__ 
 // FP32 vertical-line solve fused with the inner update (as k_update_line).
 template <int PROJ>
 __global__ void __launch_bounds__(LINE_UCOLS) k32_update_line(Geom g, const float* __restrict__ F,
-                                                            float* __restrict__ d, float* __restrict__ r,
+                                                            double* __restrict__ x, float* __restrict__ r,
                                                             const float* __restrict__ p, const float* __restrict__ w,
                                                             float* __restrict__ z, const double* __restrict__ m,
-                                                            double* partials, PcgScalars* sc, int update) {
+                                                            double* partials, PcgScalars* sc, int mode) {
+  // mode 0: first step (z, rho, beta = 0); 1: a full iteration (x, r update, z, rho, beta);
+  // 2: finish an iteration after a residual replacement (z, rho_new, beta = rho_new / rho)
   extern __shared__ float smf[];
-  if (update && sc_done(sc)) return;
-  const float alpha = update ? (float)sc->alpha : 0.f;
+  const int update = mode == 1;
+  if (mode != 0 && sc_done(sc)) return;
+  const double alpha_d = update ? sc->alpha : 0.0;
+  const float alpha = (float)alpha_d;
   const int nz = g.nz, ld = nz + 1;
   const int ncols = g.ncols;
   const int n = (int)g.n;
@@ -1268,7 +1319,7 @@ __global__ void __launch_bounds__(LINE_UCOLS) k32_update_line(Geom g, const floa
       const int row = row0 + i;
       float ri = r[row];
       if (update) {
-        d[row] = fmaf(alpha, p[row], d[row]);
+        x[row] = fma(alpha_d, (double)p[row], x[row]);
         ri = fmaf(-alpha, w[row], ri);
         r[row] = ri;
       }
@@ -1311,11 +1362,19 @@ __global__ void __launch_bounds__(LINE_UCOLS) k32_update_line(Geom g, const floa
   if (grid_sum<4>(v, partials, &sc->count[4]) && threadIdx.x == 0) {
     const double c = PROJ ? v[2] / sc->one_m : 0.0;
     const double rho_new = v[1] - c * v[3];
-    if (!update) {
+    if (mode == 0) {
       sc->proj_c = c;
       sc->rho = rho_new;
       sc->beta = 0.0;
       if ((!(rho_new > 0.0) || !isfinite(rho_new)) && !sc->done) {
+        sc->status = PM_BREAKDOWN;
+        sc->done = 1;
+      }
+    } else if (mode == 2) {
+      sc->proj_c = c;
+      sc->beta = rho_new / sc->rho;
+      sc->rho = rho_new;
+      if (!(rho_new > 0.0) || !isfinite(rho_new)) {
         sc->status = PM_BREAKDOWN;
         sc->done = 1;
       }
@@ -1327,6 +1386,8 @@ __global__ void __launch_bounds__(LINE_UCOLS) k32_update_line(Geom g, const floa
       } else if (sc->iter >= sc->max_iter) {
         sc->status = PM_NOT_CONVERGED;
         sc->done = 1;
+      } else if (v[0] <= sc->aux[2]) {
+        sc->done = 2;
       } else {
         sc->proj_c = c;
         sc->beta = rho_new / sc->rho;
@@ -1415,18 +1476,22 @@ int ensure_mixed(pm_operator* op, int which, int precision, int prec, cudaStream
   const int vs = which_valset(which);
   const int64_t nv = (int64_t)NSLOT * op->npad;
   const int G = grid_for(nv, TPB, op->num_sms);
+  const int zero_rs = vs == VS_KI ? 1 : 0;
+  const int Gr = grid_for(op->npad, TPB, op->num_sms);
+  (void)G;
   if (precision == PM_FP32_REFINE && !op->d_val32[vs]) {
     int st = cuda_check(cudaMalloc((void**)&op->d_val32[vs], nv * sizeof(float)), "cudaMalloc fp32 values");
     if (st) return st;
     op->device_bytes += nv * 4;
-    k_cvt<float><<<G, TPB, 0, s>>>(nv, op->d_val[vs], op->d_val32[vs]);
+    k_cvt_diff<float><<<Gr, TPB, 0, s>>>(op->n, op->npad, op->d_val[vs], op->d_val32[vs], zero_rs);
     count_launch();
   }
   if (precision == PM_BF16_REFINE && !op->d_val16[vs]) {
     int st = cuda_check(cudaMalloc((void**)&op->d_val16[vs], nv * sizeof(uint16_t)), "cudaMalloc bf16 values");
     if (st) return st;
     op->device_bytes += nv * 2;
-    k_cvt<__nv_bfloat16><<<G, TPB, 0, s>>>(nv, op->d_val[vs], reinterpret_cast<__nv_bfloat16*>(op->d_val16[vs]));
+    k_cvt_diff<__nv_bfloat16><<<Gr, TPB, 0, s>>>(op->n, op->npad, op->d_val[vs],
+                                                reinterpret_cast<__nv_bfloat16*>(op->d_val16[vs]), zero_rs);
     count_launch();
   }
   if (prec == PM_PREC_LINE && !op->d_line32[which]) {
@@ -1466,7 +1531,8 @@ double bytes_per_inner(const pm_operator* op, int prec, int vbytes) {
 }
 
 template <int MASKC, typename TV>
-void inner_iter(pm_operator* op, int which, const TV* val32, bool proj, int prec, const float* dinv32, cudaStream_t s) {
+void inner_iter(pm_operator* op, int which, const TV* val32, bool proj, int prec, const float* dinv32, double* x,
+                cudaStream_t s) {
   SolveCtx* c = op->ctx;
   Geom g = geom_of(op);
   const int G = grid_for(op->n, TPB, op->num_sms);
@@ -1481,10 +1547,10 @@ void inner_iter(pm_operator* op, int which, const TV* val32, bool proj, int prec
     {
       KtScope t(PM_KT_LINE, 1, s);
       if (proj)
-        k32_update_line<1><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], c->d32, c->r32, c->p32, c->w32,
+        k32_update_line<1><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], x, c->r32, c->p32, c->w32,
                                                           c->z32, op->d_m, c->partials, c->sc_in, 1);
       else
-        k32_update_line<0><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], c->d32, c->r32, c->p32, c->w32,
+        k32_update_line<0><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], x, c->r32, c->p32, c->w32,
                                                           c->z32, op->d_m, c->partials, c->sc_in, 1);
     }
     {
@@ -1495,7 +1561,7 @@ void inner_iter(pm_operator* op, int which, const TV* val32, bool proj, int prec
   } else if (prec == PM_PREC_IC0) {
     {
       KtScope t(PM_KT_UPDATE, 1, s);
-      k32_update<0, 0><<<G, TPB, 0, s>>>(op->n, c->d32, c->r32, c->p32, c->w32, dinv32, op->d_m, c->partials, c->sc_in);
+      k32_update<0, 0><<<G, TPB, 0, s>>>(op->n, x, c->r32, c->p32, c->w32, dinv32, op->d_m, c->partials, c->sc_in);
     }
     {
       KtScope t(PM_KT_IC0, 16, s);
@@ -1511,8 +1577,8 @@ void inner_iter(pm_operator* op, int which, const TV* val32, bool proj, int prec
   } else {
     {
       KtScope t(PM_KT_UPDATE, 1, s);
-      if (proj) k32_update<1, 1><<<G, TPB, 0, s>>>(op->n, c->d32, c->r32, c->p32, c->w32, dinv32, op->d_m, c->partials, c->sc_in);
-      else k32_update<0, 1><<<G, TPB, 0, s>>>(op->n, c->d32, c->r32, c->p32, c->w32, dinv32, op->d_m, c->partials, c->sc_in);
+      if (proj) k32_update<1, 1><<<G, TPB, 0, s>>>(op->n, x, c->r32, c->p32, c->w32, dinv32, op->d_m, c->partials, c->sc_in);
+      else k32_update<0, 1><<<G, TPB, 0, s>>>(op->n, x, c->r32, c->p32, c->w32, dinv32, op->d_m, c->partials, c->sc_in);
     }
     {
       KtScope t(PM_KT_PUPDATE, 1, s);
@@ -1522,19 +1588,47 @@ void inner_iter(pm_operator* op, int which, const TV* val32, bool proj, int prec
   }
 }
 
-void inner_first(pm_operator* op, int which, bool proj, int prec, const float* dinv32, cudaStream_t s) {
+// z = P^{-1} r32, rho = (r, z'). reset_p (first step): beta = 0, p = z'. Otherwise the step
+// that a residual replacement interrupted is finished: beta = rho_new / rho_old, p = z' + beta p.
+void inner_first(pm_operator* op, int which, bool proj, int prec, const float* dinv32, double* x, bool reset_p,
+                 cudaStream_t s) {
   SolveCtx* c = op->ctx;
   Geom g = geom_of(op);
   const int G = grid_for(op->n, TPB, op->num_sms);
+  if (!reset_p) {
+    if (prec == PM_PREC_LINE) {
+      const int64_t ntiles = (op->ncols + LINE_UCOLS - 1) / LINE_UCOLS;
+      int grid = (int)std::min<int64_t>(ntiles, std::min<int64_t>((int64_t)op->num_sms * 8, MAX_GRID));
+      const size_t smem = (size_t)LINE_UCOLS * (op->nz + 1) * sizeof(float);
+      if (proj)
+        k32_update_line<1><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], x, c->r32, c->p32, c->w32, c->z32,
+                                                          op->d_m, c->partials, c->sc_in, 2);
+      else
+        k32_update_line<0><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], x, c->r32, c->p32, c->w32, c->z32,
+                                                          op->d_m, c->partials, c->sc_in, 2);
+      k32_pupd<1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, c->p32, c->sc_in, 0);
+    } else if (prec == PM_PREC_IC0) {
+      ic0_apply32(op, which, c->r32, c->z32, c->sc_in, 0, s);
+      if (proj) k32_rho<1, 1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, op->d_m, c->partials, c->sc_in, 0);
+      else k32_rho<0, 1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, op->d_m, c->partials, c->sc_in, 0);
+      k32_pupd<1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, c->p32, c->sc_in, 0);
+    } else {
+      if (proj) k32_rho<1, 0><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, nullptr, op->d_m, c->partials, c->sc_in, 0);
+      else k32_rho<0, 0><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, nullptr, op->d_m, c->partials, c->sc_in, 0);
+      k32_pupd<0><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, nullptr, c->p32, c->sc_in, 0);
+    }
+    count_launch(2);
+    return;
+  }
   if (prec == PM_PREC_LINE) {
     const int64_t ntiles = (op->ncols + LINE_UCOLS - 1) / LINE_UCOLS;
     int grid = (int)std::min<int64_t>(ntiles, std::min<int64_t>((int64_t)op->num_sms * 8, MAX_GRID));
     const size_t smem = (size_t)LINE_UCOLS * (op->nz + 1) * sizeof(float);
     if (proj)
-      k32_update_line<1><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], c->d32, c->r32, c->p32, c->w32,
+      k32_update_line<1><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], x, c->r32, c->p32, c->w32,
                                                         c->z32, op->d_m, c->partials, c->sc_in, 0);
     else
-      k32_update_line<0><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], c->d32, c->r32, c->p32, c->w32,
+      k32_update_line<0><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], x, c->r32, c->p32, c->w32,
                                                         c->z32, op->d_m, c->partials, c->sc_in, 0);
     k32_pupd<1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, c->p32, c->sc_in, 1);
   } else if (prec == PM_PREC_IC0) {
@@ -1579,8 +1673,8 @@ int mixed_run(pm_operator* op, int which, const double* b, double* x, const pm_s
     count_launch();
     dinv32 = c->z32;
   }
-  const double inner_rtol = o->inner_rtol > 0.0 ? o->inner_rtol
-                                                : (std::is_same<TV, float>::value ? 1e-4 : 1e-2);
+  // residual replacement each time the recursive residual has dropped by this factor
+  const double inner_rtol = o->inner_rtol > 0.0 ? o->inner_rtol : 1e-2;
   const int G = grid_for(op->n, TPB, op->num_sms);
   PcgScalars init;
   std::memset(&init, 0, sizeof(init));
@@ -1607,47 +1701,69 @@ int mixed_run(pm_operator* op, int which, const double* b, double* x, const pm_s
     k_fill<<<G, TPB, 0, s>>>(x, op->n, 0.0);
     count_launch();
   } else {
+    // One CG process with reliable updates: x in FP64; r, p, w, z in FP32; dots, alpha and beta
+    // in FP64. The FP32 recursive residual is replaced by the FP64 true residual b - A x each
+    // time it has dropped by inner_rtol since the last replacement, and whenever it claims
+    // convergence; the search direction is kept, so the Krylov process is never restarted.
+    const double rr_drop = inner_rtol * inner_rtol;
+    PcgScalars in;
+    std::memset(&in, 0, sizeof(in));
+    in.one_m = op->one_m;
+    in.max_iter = o->max_iter;
+    in.tol2 = c->sc_host->tol2;
+    in.bb = bb;
+    in.aux[2] = rr_drop * c->sc_host->rr;   // replacement threshold on the recursive (r, r)
+    if ((st = cuda_check(cudaMemcpyAsync(c->sc_in, &in, sizeof(in), cudaMemcpyHostToDevice, s), "scalars"))) return st;
+    k32_from64<<<G, TPB, 0, s>>>(op->n, c->r, c->r32);
+    count_launch();
+    inner_first(op, which, proj, prec, dinv32, x, true, s);
+    if ((st = read_inner(c, s))) return st;
+    int64_t issued = 0;
+    const int32_t zero = 0;
     for (;;) {
-      launch_residual<MASKC>(op, val64, bw, x, o->rtol, 1, s);   // FP64 true residual into c->r
-      if ((st = read_scalars(c, s))) return st;
-      rel_true = std::sqrt(c->sc_host->aux[0] / bb);
-      rel_floor = std::ldexp(1.0, -53) * std::sqrt(c->sc_host->aux[1] / bb);
-      bytes += (double)op->n * (15 * 8 + 3 * 8);
-      if (rel_true <= std::max(o->rtol, rel_floor)) break;
-      if (inner_total >= o->max_iter || outer >= 64) {
-        status = PM_NOT_CONVERGED;
-        break;
-      }
-      // inner solve A32 d = r in FP32
-      PcgScalars in;
-      std::memset(&in, 0, sizeof(in));
-      in.one_m = op->one_m;
-      in.max_iter = o->max_iter - inner_total;
-      if ((st = cuda_check(cudaMemcpyAsync(c->sc_in, &in, sizeof(in), cudaMemcpyHostToDevice, s), "scalars"))) return st;
-      k32_start<<<G, TPB, 0, s>>>(op->n, c->r, c->r32, c->d32, inner_rtol, c->partials, c->sc_in);
-      count_launch();
-      inner_first(op, which, proj, prec, dinv32, s);
-      if ((st = read_inner(c, s))) return st;
-      int64_t issued = 0;
       int chunk = 4;
       while (!c->sc_in_host->done) {
-        if (issued > (int64_t)in.max_iter + 4096) return set_error(PM_ECUDA, "mixed PCG: device never reported completion");
-        for (int it = 0; it < chunk; ++it) inner_iter<MASKC, TV>(op, which, val32, proj, prec, dinv32, s);
+        if (issued > (int64_t)o->max_iter + 4096) return set_error(PM_ECUDA, "mixed PCG: device never reported completion");
+        for (int it = 0; it < chunk; ++it) inner_iter<MASKC, TV>(op, which, val32, proj, prec, dinv32, x, s);
         issued += chunk;
         if ((st = read_inner(c, s))) return st;
         if (chunk < 64) chunk *= 2;
       }
-      const int its = c->sc_in_host->iter;
-      inner_total += its;
-      bytes += its * bytes_per_inner(op, prec, vbytes);
-      if (c->sc_in_host->status == PM_BREAKDOWN && its == 0) {
+      // FP64 true residual into c->r
+      launch_residual<MASKC>(op, val64, bw, x, o->rtol, 1, s);
+      if ((st = read_scalars(c, s))) return st;
+      ++outer;
+      bytes += (double)op->n * (15 * 8 + 3 * 8);
+      rel_true = std::sqrt(c->sc_host->aux[0] / bb);
+      rel_floor = std::ldexp(1.0, -53) * std::sqrt(c->sc_host->aux[1] / bb);
+      if (rel_true <= std::max(o->rtol, rel_floor)) break;
+      if (c->sc_in_host->status == PM_BREAKDOWN) {
         status = PM_BREAKDOWN;
         break;
       }
-      k_add_f32<<<G, TPB, 0, s>>>(op->n, x, c->d32);
+      if (c->sc_in_host->iter >= o->max_iter) {
+        status = PM_NOT_CONVERGED;
+        break;
+      }
+      // residual replacement: r32 = (float)(b - A x); the interrupted step is finished with it
+      const double thr = rr_drop * c->sc_host->aux[0];
+      if ((st = cuda_check(cudaMemcpyAsync(&c->sc_in->done, &zero, sizeof(zero), cudaMemcpyHostToDevice, s), "scalars")))
+        return st;
+      if ((st = cuda_check(cudaMemcpyAsync(&c->sc_in->aux[2], &thr, sizeof(thr), cudaMemcpyHostToDevice, s), "scalars")))
+        return st;
+      k32_from64<<<G, TPB, 0, s>>>(op->n, c->r, c->r32);
       count_launch();
-      ++outer;
+      // FP32 values perturb A at rounding level: keep the Krylov process (reliable update) on the
+      // pressure system. BF16 values perturb it by ~0.4%, so CG runs on a different operator:
+      // restart from the true residual instead (iterative refinement with an approximate inner
+      // solve). The Dirichlet-eliminated velocity systems also restart: continuing their Krylov
+      // process across a replacement converged far slower on the ocean basins.
+      const bool restart = !std::is_same<TV, float>::value || MASKC >= 0;
+      inner_first(op, which, proj, prec, dinv32, x, restart, s);
+      if ((st = read_inner(c, s))) return st;
     }
+    inner_total = c->sc_in_host->iter;
+    bytes += inner_total * bytes_per_inner(op, prec, vbytes);
   }
   if (proj) {
     k_cg_press_sums<<<G, TPB, 0, s>>>(op->n, b, x, op->d_m, 1, c->partials, c->sc);
