@@ -246,7 +246,8 @@ def run_ours(args):
         api.KT_UPDATE: n * (4 * 8 + 2 * 8),           # IC0 path: x, r, p, w read; x, r written
         api.KT_PUPDATE: n * (3 * 8 + 8) / 2,          # (r, z) dot + p update, two launches
         api.KT_IC0: n * (2 * 8 * 8 + 4 * 8) / 16,     # F (8 per row per sweep), r/y/z, per launch
-        api.KT_LINE: n * (8 + 3 * 8 + 8 + 8),         # r, 3 Thomas factors, z, m
+        # fused update + line solve: x, r read+write, p, w, 3 Thomas factors, z, r again, m
+        api.KT_LINE: n * (2 * 8 + 2 * 8 + 8 + 8 + 3 * 8 + 8 + 8 + 8),
     }
     names = {api.KT_SPMV: "k_cg_spmv", api.KT_UPDATE: "k_cg_update", api.KT_PUPDATE: "k_cg_rho+k_cg_pupd",
              api.KT_IC0: "k_ic0_sweep", api.KT_LINE: "k_line_rho"}
@@ -306,13 +307,17 @@ def run_ours(args):
     if not args.no_mixed:
         ref = [t.clone() for t in st.get()]
         for label, prc in (("fp32", pm.FP32_REFINE), ("bf16", pm.BF16_REFINE)):
-            vm = pm.Options(rtol=1e-8, prec=pm.PREC_IC0, precision=prc, max_iter=500000)
-            pmo = pm.Options(rtol=1e-8, prec=pm.PREC_LINE, precision=prc, max_iter=500000)
+            vm = pm.Options(rtol=1e-8, prec=pm.PREC_IC0, precision=prc, max_iter=60000)
+            pmo = pm.Options(rtol=1e-8, prec=pm.PREC_LINE, precision=prc, max_iter=60000)
 
             def mstep():
                 st.set(step_index=0)
-                return pm.project_step(op, st, t1, t2, vm, pmo)
-            mstep()
+                return pm.project_step(op, st, t1, t2, vm, pmo, allow_not_converged=True)
+            try:
+                mstep()
+            except pm.PMError as ex:
+                mixed[label] = {"error": str(ex)[:200]}
+                continue
             torch.cuda.synchronize()
             k_m = max(2, min(args.steps, 3))
             g0 = torch.cuda.Event(enable_timing=True)
@@ -334,6 +339,8 @@ def run_ours(args):
                             "inner_iters": [int(s.iters) for s in ms_stats[:4]],
                             "outer_iters": [int(s.outer_iters) for s in ms_stats[:4]],
                             "rel_residual_true": [float(f"{s.rel_residual_true:.3e}") for s in ms_stats[:4]],
+                            "rel_residual_floor": [float(f"{s.rel_residual_floor:.3e}") for s in ms_stats[:4]],
+                            "status": [int(s.status) for s in ms_stats[:4]],
                             "per_field_max_rel_err_vs_fp64": {k: float(f"{v:.3e}") for k, v in errs.items()}}
 
     cpu = None

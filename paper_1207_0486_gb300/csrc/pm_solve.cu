@@ -584,25 +584,28 @@ __global__ void __launch_bounds__(LINE_TPB) k_line_rho(Geom g, const double* __r
 //   z = P^{-1} r column by column (one thread per column, in place), then the reductions
 //   (r, r), (r, z) [m'z, 1'r]. The last block tests convergence on (r, r) and forms beta, as
 //   k_cg_update + k_line_rho would; the z of the converged iteration is simply not used.
-constexpr int LINE_UCOLS = 128;
+constexpr int LINE_UCOLS = 128;   // FP32 fused kernel: columns (= threads) per block
+constexpr int LINE_FCOLS = 64;    // FP64 fused kernel: columns per block (128 threads stage them)
+constexpr int LINE_FTPB = 128;
 
-template <int PROJ>
-__global__ void __launch_bounds__(LINE_UCOLS) k_update_line(Geom g, const double* __restrict__ F,
-                                                          double* __restrict__ x, double* __restrict__ r,
-                                                          const double* __restrict__ p, const double* __restrict__ w,
-                                                          double* __restrict__ z, const double* __restrict__ m,
-                                                          double* partials, PcgScalars* sc) {
+// NZ > 0: compile-time column height (shifts instead of divisions); NZ == 0: g.nz at run time.
+template <int PROJ, int NZ>
+__global__ void __launch_bounds__(LINE_FTPB) k_update_line(Geom g, const double* __restrict__ F,
+                                                         double* __restrict__ x, double* __restrict__ r,
+                                                         const double* __restrict__ p, const double* __restrict__ w,
+                                                         double* __restrict__ z, const double* __restrict__ m,
+                                                         double* partials, PcgScalars* sc) {
   extern __shared__ double smem[];
   if (sc_done(sc)) return;
   const double alpha = sc->alpha;
-  const int nz = g.nz, ld = nz + 1;
+  const int nz = NZ > 0 ? NZ : g.nz, ld = nz + 1;
   const int ncols = g.ncols;
   const int n = (int)g.n;
-  const int ntiles = (ncols + LINE_UCOLS - 1) / LINE_UCOLS;
+  const int ntiles = (ncols + LINE_FCOLS - 1) / LINE_FCOLS;
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int c0 = tile * LINE_UCOLS;
-    const int cc = min(LINE_UCOLS, ncols - c0);
+    const int c0 = tile * LINE_FCOLS;
+    const int cc = min(LINE_FCOLS, ncols - c0);
     const int row0 = c0 * nz;
     const int rows = cc * nz;
     for (int i = threadIdx.x; i < rows; i += blockDim.x) {
@@ -671,22 +674,27 @@ __global__ void __launch_bounds__(LINE_UCOLS) k_update_line(Geom g, const double
 void update_line(pm_operator* op, int which, bool proj, double* x, cudaStream_t s) {
   SolveCtx* c = op->ctx;
   Geom g = geom_of(op);
-  const int64_t ntiles = (op->ncols + LINE_UCOLS - 1) / LINE_UCOLS;
-  int grid = (int)std::min<int64_t>(ntiles, std::min<int64_t>((int64_t)op->num_sms * 8, MAX_GRID));
+  const int64_t ntiles = (op->ncols + LINE_FCOLS - 1) / LINE_FCOLS;
+  int grid = (int)std::min<int64_t>(ntiles, std::min<int64_t>((int64_t)op->num_sms * 16, MAX_GRID));
   if (grid < 1) grid = 1;
-  const size_t smem = (size_t)LINE_UCOLS * (op->nz + 1) * sizeof(double);
+  const size_t smem = (size_t)LINE_FCOLS * (op->nz + 1) * sizeof(double);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_update_line<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_update_line<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_update_line<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_update_line<1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
-  if (proj)
-    k_update_line<1><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line[which], x, c->r, c->p, c->w, c->z, op->d_m,
-                                                    c->partials, c->sc);
-  else
-    k_update_line<0><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line[which], x, c->r, c->p, c->w, c->z, op->d_m,
-                                                    c->partials, c->sc);
+  const double* F = op->d_line[which];
+#define PM_UL(P, NZ) \
+  k_update_line<P, NZ><<<grid, LINE_FTPB, smem, s>>>(g, F, x, c->r, c->p, c->w, c->z, op->d_m, c->partials, c->sc)
+  if (op->nz == 32) {
+    if (proj) PM_UL(1, 32);
+    else PM_UL(0, 32);
+  } else {
+    if (proj) PM_UL(1, 0);
+    else PM_UL(0, 0);
+  }
+#undef PM_UL
   count_launch();
 }
 
@@ -1720,6 +1728,8 @@ int mixed_run(pm_operator* op, int which, const double* b, double* x, const pm_s
     if ((st = read_inner(c, s))) return st;
     int64_t issued = 0;
     const int32_t zero = 0;
+    int stalled = 0;
+    double prev_true = 1e300;
     for (;;) {
       int chunk = 4;
       while (!c->sc_in_host->done) {
@@ -1737,6 +1747,13 @@ int mixed_run(pm_operator* op, int which, const double* b, double* x, const pm_s
       rel_true = std::sqrt(c->sc_host->aux[0] / bb);
       rel_floor = std::ldexp(1.0, -53) * std::sqrt(c->sc_host->aux[1] / bb);
       if (rel_true <= std::max(o->rtol, rel_floor)) break;
+      // stagnation: three replacements in a row that did not halve the true residual
+      stalled = rel_true > 0.5 * prev_true ? stalled + 1 : 0;
+      prev_true = rel_true;
+      if (stalled >= 3) {
+        status = PM_NOT_CONVERGED;
+        break;
+      }
       if (c->sc_in_host->status == PM_BREAKDOWN) {
         status = PM_BREAKDOWN;
         break;
@@ -1753,13 +1770,11 @@ int mixed_run(pm_operator* op, int which, const double* b, double* x, const pm_s
         return st;
       k32_from64<<<G, TPB, 0, s>>>(op->n, c->r, c->r32);
       count_launch();
-      // FP32 values perturb A at rounding level: keep the Krylov process (reliable update) on the
-      // pressure system. BF16 values perturb it by ~0.4%, so CG runs on a different operator:
-      // restart from the true residual instead (iterative refinement with an approximate inner
-      // solve). The Dirichlet-eliminated velocity systems also restart: continuing their Krylov
-      // process across a replacement converged far slower on the ocean basins.
-      const bool restart = !std::is_same<TV, float>::value || MASKC >= 0;
-      inner_first(op, which, proj, prec, dinv32, x, restart, s);
+      // Restart from the true residual (iterative refinement with an approximate inner solve).
+      // Continuing the Krylov process across the replacement (reliable update: finish the
+      // interrupted step with the replaced residual) is implemented in inner_first but not used:
+      // on the ocean basins it converged far slower than the same scheme emulated on the CPU.
+      inner_first(op, which, proj, prec, dinv32, x, true, s);
       if ((st = read_inner(c, s))) return st;
     }
     inner_total = c->sc_in_host->iter;
