@@ -188,6 +188,37 @@ int pm_pcg_solve(pm_operator* op, pm_which which, const double* b, double* x,
 int pm_pcg_solve_noalloc(pm_operator* op, pm_which which, const double* b, double* x,
                          const pm_solve_opts* opts, pm_solve_stats* stats, pm_stream stream);
 
+/* ---- batched solves (many basins x right-hand sides in one persistent launch) ---------------- */
+
+/* A batch of independent systems (operator ops[i] with which[i]), solved together by one
+ * persistent cooperative kernel per quantum of iterations, captured once in a CUDA graph and
+ * replayed: PCG of the Section 5 remark for every system, all systems advancing together, each
+ * with its own alpha / beta / convergence. Supported: PM_PREC_JACOBI, PM_PREC_LINE (PM_PREC_NONE
+ * maps to Jacobi); PM_FP64, or PM_FP32_REFINE (FP32 difference-form values and vectors, FP64 x,
+ * dots and true-residual restarts). Starts from x = 0; the pressure zero-mean reading applies
+ * to PM_OP_PRESSURE entries. autotune != 0 times the tile width (columns per tile: 16, 32, 64) x
+ * block size (128, 256) on this batch once and caches the choice per size bucket.
+ * Grid waits are bounded: an expired wait returns PM_TIMEOUT. The batch keeps its own workspace;
+ * the operators must outlive it. */
+int pm_batch_create(pm_operator* const* ops, const pm_which* which, int32_t count,
+                    const pm_solve_opts* opts, int32_t autotune, pm_batch** out, pm_stream stream);
+/* Solve all systems: b[i], x[i] device vectors of ops[i]'s length. stats: NULL or count entries.
+ * Synchronises the stream. */
+int pm_batch_solve(pm_batch* batch, const double* const* b, double* const* x, pm_solve_stats* stats,
+                   pm_stream stream);
+int pm_batch_info(const pm_batch* batch, int32_t* tile_cols, int32_t* block, int32_t* grid,
+                  int64_t* ntiles);
+void pm_batch_destroy(pm_batch* batch);
+/* Test aid for failure detection: launches a two-block cooperative kernel in which one block
+ * leaves without reaching the grid barrier, so the other block's bounded wait expires (about 2 s).
+ * Returns the status that wait recorded: PM_TIMEOUT. Nothing faults, traps or hangs, and the
+ * context stays usable. */
+int pm_debug_barrier_timeout(pm_stream stream);
+/* One-shot: create (no autotuning), solve, destroy. */
+int pm_pcg_solve_batched(pm_operator* const* ops, const pm_which* which, const double* const* b,
+                         double* const* x, int32_t count, const pm_solve_opts* opts,
+                         pm_solve_stats* stats, pm_stream stream);
+
 /* ---- projection step ---------------------------------------------------------------------- */
 
 /* Time-step state u^k, u^{k-1}, p^k (device, owned by the handle). Created at rest:

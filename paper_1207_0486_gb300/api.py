@@ -87,6 +87,13 @@ SIGNATURES = {
     "pm_status_string": (ctypes.c_char_p, [_I]),
     "pm_last_error": (_I, [ctypes.c_char_p, ctypes.c_int32]),
     "pm_kernel_launch_count": (ctypes.c_int64, []),
+    "pm_batch_create": (_I, [_P, _P, ctypes.c_int32, ctypes.POINTER(SolveOpts), ctypes.c_int32,
+                             ctypes.POINTER(_P), _P]),
+    "pm_batch_solve": (_I, [_P, _P, _P, _P, _P]),
+    "pm_batch_info": (_I, [_P, _P, _P, _P, _P]),
+    "pm_batch_destroy": (None, [_P]),
+    "pm_pcg_solve_batched": (_I, [_P, _P, _P, _P, ctypes.c_int32, ctypes.POINTER(SolveOpts), _P, _P]),
+    "pm_debug_barrier_timeout": (_I, [_P]),
     "pm_kernel_timing": (_I, [ctypes.c_int32]),
     "pm_kernel_timing_get": (_I, [ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
 }
@@ -333,3 +340,55 @@ def project_step(op: Operator, state: State, theta1=None, theta2=None, vel: Opti
 
 def kernel_launch_count() -> int:
     return int(load().pm_kernel_launch_count())
+
+
+class Batch:
+    """A batch of independent systems solved by one persistent, graph-captured kernel (pm_batch)."""
+
+    def __init__(self, ops: Sequence[Operator], which: Sequence[int], opts: Options = None,
+                 autotune: bool = False, stream=None):
+        opts = opts or Options(prec=PREC_LINE)
+        self.ops = list(ops)
+        self.which = list(which)
+        n = len(self.ops)
+        hops = (ctypes.c_void_p * n)(*[o.handle.value if isinstance(o.handle, ctypes.c_void_p) else o.handle
+                                       for o in self.ops])
+        hw = (ctypes.c_int * n)(*self.which)
+        o = opts.c()
+        h = ctypes.c_void_p()
+        _check(load().pm_batch_create(hops, hw, n, ctypes.byref(o), 1 if autotune else 0, ctypes.byref(h),
+                                      _stream(stream)), "batch_create")
+        self.handle = h
+        self._keep = (hops, hw)
+
+    def info(self):
+        tc, blk, grid = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        nt = ctypes.c_int64()
+        _check(load().pm_batch_info(self.handle, ctypes.byref(tc), ctypes.byref(blk), ctypes.byref(grid),
+                                    ctypes.byref(nt)), "batch_info")
+        return {"tile_cols": tc.value, "block": blk.value, "grid": grid.value, "tiles": nt.value}
+
+    def solve(self, bs, xs, stream=None, allow_not_converged=False):
+        n = len(self.ops)
+        pb = (ctypes.c_void_p * n)(*[_dptr(b, o.n, "b").value for b, o in zip(bs, self.ops)])
+        px = (ctypes.c_void_p * n)(*[_dptr(x, o.n, "x").value for x, o in zip(xs, self.ops)])
+        stats = (SolveStats * n)()
+        r = load().pm_batch_solve(self.handle, pb, px, stats, _stream(stream))
+        _check(r, "batch_solve", allow=(PM_NOT_CONVERGED,) if allow_not_converged else ())
+        return [stats[i] for i in range(n)]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().pm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def debug_barrier_timeout(stream=None) -> int:
+    """Status of a deliberately expired bounded grid wait (PM_TIMEOUT expected)."""
+    return int(load().pm_debug_barrier_timeout(_stream(stream)))

@@ -11,7 +11,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpm_gb300.so")
-SOURCES = ["pm_api.cu", "pm_mesh.cu", "pm_assemble.cu", "pm_solve.cu", "pm_step.cu", "pm_noalloc.cu"]
+SOURCES = ["pm_api.cu", "pm_mesh.cu", "pm_assemble.cu", "pm_solve.cu", "pm_step.cu", "pm_noalloc.cu",
+           "pm_batch.cu"]
+# The persistent batched kernel reads data other blocks write during the launch: plain global
+# loads in that file are cached in L2 only (ld.global.cg), never in the non-coherent L1.
+EXTRA = {"pm_batch.cu": ["-Xptxas", "-dlcm=cg"]}
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -29,7 +33,7 @@ def _flags():
 
 def _compile(src: str, verbose_ptxas: bool) -> str:
     obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc()] + _flags() + ["-c", os.path.join(CSRC, src), "-o", obj]
+    cmd = [nvcc()] + _flags() + EXTRA.get(src, []) + ["-c", os.path.join(CSRC, src), "-o", obj]
     if verbose_ptxas:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -1853,6 +1853,17 @@ int pcg_solve(pm_operator* op, int which, const double* b, double* x, const pm_s
   }
 }
 
+// Everything a batched solve reads from one operator: Jacobi diagonals, line factors, and for
+// FP32 the difference-form values and FP32 factors.
+int prepare_for_batch(pm_operator* op, int which, int prec, int precision, cudaStream_t s) {
+  int st = ensure_ctx(op);
+  if (st) return st;
+  if ((st = launch_dinv(op, which, s))) return st;
+  if (prec == PM_PREC_LINE && (st = line_factor(op, which, s))) return st;
+  if (precision != PM_FP64 && (st = ensure_mixed(op, which, precision, prec, s))) return st;
+  return PM_OK;
+}
+
 }  // namespace pm
 
 extern "C" int pm_kernel_timing(int32_t enable) {

@@ -1,0 +1,128 @@
+"""Batched persistent PCG: every system of a batch matches its solo solve and the oracle, results
+do not depend on what else is in the batch, and a bounded grid wait reports PM_TIMEOUT."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from gpu_util import theta_basin  # noqa: E402
+from oracle import fem, pcg as opcg  # noqa: E402
+from test_oracle_fem import small_basin  # noqa: E402
+from workloads import box_basin, ocean_basin, random_vector  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+import paper_1207_0486_gb300 as pm  # noqa: E402
+
+_cache = {}
+
+
+def case(name):
+    if name not in _cache:
+        b = {"box16": lambda: theta_basin(box_basin()), "small": small_basin,
+             "box24": lambda: box_basin(nh=24, nz=12),
+             "ocean48": lambda: ocean_basin(nx=48, ny=40, nz=9, dx=1e5)}[name]()
+        _cache[name] = (b, pm.assemble_operator(b), fem.assemble(b))
+    return _cache[name]
+
+
+def rhs_for(name, which, seed):
+    b, op, ops = case(name)
+    r = random_vector(op.n, seed)
+    if which != pm.OP_PRESSURE:
+        c = which - (pm.OP_VEL1_U1 if which >= pm.OP_VEL1_U1 else pm.OP_VEL_U1)
+        r[ops.mesh.dirichlet[c]] = 0.0
+    return r
+
+
+ENTRIES = [("box16", pm.OP_VEL_U1), ("box16", pm.OP_VEL_U2), ("box16", pm.OP_VEL_U3), ("box16", pm.OP_PRESSURE),
+           ("small", pm.OP_VEL1_U1), ("small", pm.OP_PRESSURE), ("box24", pm.OP_VEL_U3), ("box24", pm.OP_PRESSURE)]
+
+
+def oracle_matrix(ops, which):
+    if which == pm.OP_PRESSURE:
+        return ops.K_I
+    if which >= pm.OP_VEL1_U1:
+        return ops.A_u(which - pm.OP_VEL1_U1, bdf1=True)
+    return ops.A_u(which - pm.OP_VEL_U1, bdf1=False)
+
+
+def run_batch(entries, prec, precision=pm.FP64, rtol=1e-12, autotune=False):
+    opsl = [case(nm)[1] for nm, _ in entries]
+    bs = [torch.from_numpy(rhs_for(nm, w, 40 + i)).cuda() for i, (nm, w) in enumerate(entries)]
+    xs = [torch.zeros_like(b) for b in bs]
+    batch = pm.Batch(opsl, [w for _, w in entries], pm.Options(rtol=rtol, prec=prec, precision=precision,
+                                                               max_iter=200000), autotune=autotune)
+    stats = batch.solve(bs, xs)
+    info = batch.info()
+    batch.close()
+    return [x.cpu().numpy() for x in xs], stats, info
+
+
+@pytest.mark.parametrize("prec", [pm.PREC_JACOBI, pm.PREC_LINE])
+def test_batch_matches_solo_and_oracle(prec):
+    xs, stats, _ = run_batch(ENTRIES, prec)
+    for i, ((nm, w), x, st) in enumerate(zip(ENTRIES, xs, stats)):
+        b, op, ops = case(nm)
+        rhs = rhs_for(nm, w, 40 + i)
+        assert st.status == pm.PM_OK, (nm, w)
+        assert st.rel_residual_true <= max(1e-12, st.rel_residual_floor)
+        # solo solve through the regular entry point
+        xd = torch.zeros(op.n, dtype=torch.float64, device="cuda")
+        solo = op.solve(w, torch.from_numpy(rhs).cuda(), xd, pm.Options(rtol=1e-12, prec=prec, max_restarts=5),
+                        allow_not_converged=True)
+        xs_solo = xd.cpu().numpy()
+        assert np.linalg.norm(x - xs_solo) <= 1e-9 * np.linalg.norm(xs_solo), (nm, w)
+        assert abs(st.first_pass_iters - solo.first_pass_iters) <= max(2, 0.02 * solo.first_pass_iters)
+        # the oracle's solution
+        A = oracle_matrix(ops, w)
+        P = opcg.line_preconditioner(A, ops.mesh.nz) if prec == pm.PREC_LINE else opcg.jacobi_preconditioner(A)
+        if w == pm.OP_PRESSURE:
+            ref = opcg.pressure_solve(A, ops.m, rhs, rtol=1e-12, precond=P)
+        else:
+            ref = opcg.pcg(A, rhs, rtol=1e-13, precond=P)
+        assert np.linalg.norm(x - ref.x) <= 1e-9 * np.linalg.norm(ref.x), (nm, w)
+
+
+def test_batch_result_does_not_depend_on_the_mix():
+    """A system alone and inside a batch with others gives bit-identical iterates (per-system
+    reductions run over that system's tiles in a fixed order)."""
+    alone, st_a, _ = run_batch([ENTRIES[3]], pm.PREC_LINE, rtol=1e-10)
+    mixed, st_m, _ = run_batch(ENTRIES, pm.PREC_LINE, rtol=1e-10)
+    assert np.array_equal(alone[0], mixed[3])
+    assert st_a[0].iters == st_m[3].iters
+
+
+def test_batch_mixed_precision():
+    xs, stats, _ = run_batch(ENTRIES, pm.PREC_LINE, precision=pm.FP32_REFINE, rtol=1e-8)
+    for i, ((nm, w), x, st) in enumerate(zip(ENTRIES, xs, stats)):
+        b, op, ops = case(nm)
+        assert st.status == pm.PM_OK
+        assert st.rel_residual_true <= max(1e-8, st.rel_residual_floor)
+        A = oracle_matrix(ops, w)
+        rhs = rhs_for(nm, w, 40 + i)
+        if w == pm.OP_PRESSURE:
+            ref = opcg.pressure_solve(A, ops.m, rhs, rtol=1e-12)
+        else:
+            ref = opcg.pcg(A, rhs, rtol=1e-13, precond=opcg.jacobi_preconditioner(A))
+        assert np.linalg.norm(x - ref.x) <= 1e-5 * np.linalg.norm(ref.x), (nm, w)
+
+
+def test_batch_autotune_picks_a_shape():
+    xs, stats, info = run_batch(ENTRIES[:4], pm.PREC_LINE, rtol=1e-10, autotune=True)
+    assert info["tile_cols"] in (16, 32, 64) and info["block"] in (128, 256)
+    assert all(s.status == pm.PM_OK for s in stats)
+
+
+def test_batch_rejects_ic0():
+    op = case("box16")[1]
+    with pytest.raises(pm.PMError) as ei:
+        pm.Batch([op], [pm.OP_VEL_U1], pm.Options(prec=pm.PREC_IC0))
+    assert ei.value.status == pm.PM_EINVAL
+
+
+def test_bounded_grid_wait_reports_timeout_and_gpu_stays_usable():
+    assert pm.debug_barrier_timeout() == pm.PM_TIMEOUT
+    # the context still works
+    xs, stats, _ = run_batch([ENTRIES[0]], pm.PREC_JACOBI, rtol=1e-10)
+    assert stats[0].status == pm.PM_OK
