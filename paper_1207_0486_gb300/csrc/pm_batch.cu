@@ -221,8 +221,32 @@ __device__ __forceinline__ double sys_reduce(const double* part, int ntiles_tota
   return v[0];  // valid in thread 0
 }
 
+// Tiles a block owns (t = blockIdx.x mod gridDim.x) among the systems a phase works on, visited
+// system by system so that finished systems cost nothing. mode 0: ITER or REFINE (phase A),
+// 1: ITER or RESTART (phase B), 2: ITER (phase C).
+__device__ __forceinline__ bool phase_active(int state, int mode) {
+  return mode == 0 ? (state == ST_ITER || state == ST_REFINE)
+       : mode == 1 ? (state == ST_ITER || state == ST_RESTART) : state == ST_ITER;
+}
+__device__ __forceinline__ int owned_tile(const Sys* sys, const Scal* scal, int nsys, int s, int mode) {
+  const int G = gridDim.x;
+  for (; s < nsys; ++s) {
+    if (!phase_active(scal[s].state, mode)) continue;
+    const int t0 = sys[s].tile0, te = t0 + sys[s].ntiles;
+    const int t = t0 + (((int)blockIdx.x - t0) % G + G) % G;
+    if (t < te) return t;
+  }
+  return -1;
+}
+__device__ __forceinline__ int next_owned(const Sys* sys, const Scal* scal, const Tile* tiles, int nsys, int t,
+                                          int mode) {
+  const int s = tiles[t].sys;
+  const int nt = t + gridDim.x;
+  return nt < sys[s].tile0 + sys[s].ntiles ? nt : owned_tile(sys, scal, nsys, s + 1, mode);
+}
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_batch(const Sys* __restrict__ sys, Scal* scal, int nsys,
+__global__ void __launch_bounds__(256, 4) k_batch(const Sys* __restrict__ sys, Scal* scal, int nsys,
                                                const Tile* __restrict__ tiles, int ntiles, double* part, Ctl* ctl,
                                                int quantum, int init) {
   extern __shared__ unsigned char smem_raw[];
@@ -340,7 +364,7 @@ __global__ void __launch_bounds__(256) k_batch(const Sys* __restrict__ sys, Scal
   for (int it = 0; it < quantum; ++it) {
     if (*((volatile int32_t*)&ctl->active) == 0) return;
     // ---- A: SpMV + (p, w) | REFINE: FP64 residual --------------------------------------------------
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    for (int t = owned_tile(sys, scal, nsys, 0, 0); t >= 0; t = next_owned(sys, scal, tiles, nsys, t, 0)) {
       const Tile tl = tiles[t];
       const Sys& S = sys[tl.sys];
       const int state = scal[tl.sys].state;
@@ -349,6 +373,7 @@ __global__ void __launch_bounds__(256) k_batch(const Sys* __restrict__ sys, Scal
       if (state == ST_ITER) {
         const T* p = (const T*)S.p;
         T* w = (T*)S.w;
+#pragma unroll 2
         for (int i = tid; i < rows; i += blockDim.x) {
           const int row = row0 + i, col = row / nz, k = row - col * nz;
           const double wi = row_apply<T>(S.g, (const T*)S.val, p, S.maskc, row, col, k);
@@ -411,7 +436,7 @@ __global__ void __launch_bounds__(256) k_batch(const Sys* __restrict__ sys, Scal
     }
     if (!grid_barrier(ctl)) return;
     // ---- B: update + preconditioner + dots | RESTART: preconditioner + dots ---------------------------
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    for (int t = owned_tile(sys, scal, nsys, 0, 1); t >= 0; t = next_owned(sys, scal, tiles, nsys, t, 1)) {
       const Tile tl = tiles[t];
       const Sys& S = sys[tl.sys];
       const int state = scal[tl.sys].state;
@@ -518,7 +543,7 @@ __global__ void __launch_bounds__(256) k_batch(const Sys* __restrict__ sys, Scal
       for (int s = 0; s < nsys; ++s) act += scal[s].state != ST_DONE;
       ctl->active = act;
     }
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    for (int t = owned_tile(sys, scal, nsys, 0, 2); t >= 0; t = next_owned(sys, scal, tiles, nsys, t, 2)) {
       const Tile tl = tiles[t];
       const Sys& S = sys[tl.sys];
       if (scal[tl.sys].state != ST_ITER) continue;
