@@ -38,6 +38,7 @@ typedef struct CUstream_st* pm_stream; /* identical to cudaStream_t */
 typedef struct pm_operator pm_operator;
 typedef struct pm_state pm_state;
 typedef struct pm_batch pm_batch;
+typedef struct pm_server pm_server;
 
 /* ---- status codes ------------------------------------------------------------------------ */
 enum {
@@ -48,7 +49,8 @@ enum {
   PM_NOT_CONVERGED = 4, /* iteration cap reached; x holds the last iterate, stats are filled   */
   PM_BREAKDOWN = 5,     /* (p, Ap) <= 0 or non-finite, or IC0 pivot failure after 11 shifts    */
   PM_TIMEOUT = 6,       /* a bounded device-side wait ran out (persistent kernels)            */
-  PM_DISCONNECTED = 7   /* the ocean has more than one connected component                    */
+  PM_DISCONNECTED = 7,  /* the ocean has more than one connected component                    */
+  PM_EBUSY = 8          /* no free server slot; retry after a pm_server_poll frees one         */
 };
 
 /* Lateral outer walls that are artificial slip boundaries Gamma_1 (Section 2, Eq. prim_bot_1:
@@ -199,7 +201,7 @@ int pm_pcg_solve_noalloc(pm_operator* op, pm_which which, const double* b, doubl
  * to PM_OP_PRESSURE entries. autotune != 0 times the tile width (columns per tile: 16, 32, 64) x
  * block size (128, 256) on this batch once and caches the choice per size bucket.
  * Grid waits are bounded: an expired wait returns PM_TIMEOUT. The batch keeps its own workspace;
- * the operators must outlive it. */
+ * the operators must outlive it. count: 1..4096 systems. */
 int pm_batch_create(pm_operator* const* ops, const pm_which* which, int32_t count,
                     const pm_solve_opts* opts, int32_t autotune, pm_batch** out, pm_stream stream);
 /* Solve all systems: b[i], x[i] device vectors of ops[i]'s length. stats: NULL or count entries.
@@ -218,6 +220,43 @@ int pm_debug_barrier_timeout(pm_stream stream);
 int pm_pcg_solve_batched(pm_operator* const* ops, const pm_which* which, const double* const* b,
                          double* const* x, int32_t count, const pm_solve_opts* opts,
                          pm_solve_stats* stats, pm_stream stream);
+
+/* ---- continuous batching server ------------------------------------------------------------ */
+
+/* A resident solve server: a table of `slots` systems advanced together by the persistent kernel
+ * of the batched solves. Systems are admitted and retired between launches, so requests that
+ * arrive while others are on the GPU join at the next quantum instead of waiting for the batch to
+ * drain; each system's iterates depend on nothing but its own tiles (bit-identical whatever else
+ * is resident, for a fixed tile_cols and block). No paper counterpart: the paper solves one basin;
+ * this serves many basins' PCG solves (Section 5) at once.
+ * opts: as pm_batch_create (PM_PREC_JACOBI / PM_PREC_LINE / PM_PREC_NONE; PM_FP64 or
+ * PM_FP32_REFINE); every system uses them. nz_cap: the largest nz admitted (sizes shared memory).
+ * tile_cols: 16, 32 or 64 columns per tile; block: 128 or 256 threads; blocks_per_sm: resident
+ * blocks per SM of the kernel (0 = as many as fit). Errors: PM_EINVAL, PM_ENOMEM, PM_ECUDA. */
+int pm_server_create(int32_t slots, int32_t nz_cap, const pm_solve_opts* opts, int32_t tile_cols,
+                     int32_t block, int32_t blocks_per_sm, pm_server** out, pm_stream stream);
+/* Device bytes of Krylov workspace one system of `op` needs at `precision` (0 for NULL). */
+size_t pm_server_workspace_bytes(const pm_operator* op, int32_t precision);
+/* Admit one system: solve A x = b for op / which from x = 0. b, x: device vectors of op's length;
+ * work: device workspace of at least pm_server_workspace_bytes bytes, 256-byte aligned. All three
+ * are the caller's and must stay valid until the slot is returned by pm_server_poll; nothing is
+ * allocated per system except when the tile array has to grow. *slot receives the slot index.
+ * Errors: PM_EINVAL (non-symmetric which, nz > nz_cap, small or misaligned workspace),
+ * PM_EBUSY (all slots taken), PM_ENOMEM, PM_ECUDA. Async on `stream`. */
+int pm_server_admit(pm_server* srv, pm_operator* op, pm_which which, const double* b, double* x,
+                    void* work, size_t work_bytes, int32_t* slot, pm_stream stream);
+/* One launch of `quantum` iterations for every resident system (systems admitted since the last
+ * launch are initialised first). *active receives the number of systems still iterating.
+ * Synchronises the stream. An expired grid wait returns PM_TIMEOUT (the server is then unusable:
+ * destroy it). */
+int pm_server_run(pm_server* srv, int32_t quantum, int32_t* active, pm_stream stream);
+/* Retire finished systems: up to max_out of them are written to slots[] / stats[] (stats may be
+ * NULL) and their slots freed; *n_out receives the count. Host only. */
+int pm_server_poll(pm_server* srv, int32_t* slots, pm_solve_stats* stats, int32_t max_out,
+                   int32_t* n_out);
+int pm_server_info(const pm_server* srv, int32_t* tile_cols, int32_t* block, int32_t* grid,
+                   int64_t* tile_capacity, int64_t* launches);
+void pm_server_destroy(pm_server* srv);
 
 /* ---- projection step ---------------------------------------------------------------------- */
 

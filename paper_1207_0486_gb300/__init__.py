@@ -6,11 +6,11 @@ Sections 3-5) -- runs in hand-written sm_103a CUDA kernels behind the C ABI of i
 This package is the thin Python binding (`api`) and the in-tree build (`build`).
 """
 from .api import (  # noqa: F401
-    Operator, State, Options, SolveStats, PMError, Batch, debug_barrier_timeout,
+    Operator, State, Options, SolveStats, PMError, Batch, Server, debug_barrier_timeout,
     assemble_operator, pcg_solve, project_step, operator_bytes, kernel_launch_count, load,
     OP_VEL_U1, OP_VEL_U2, OP_VEL_U3, OP_PRESSURE, OP_MASS, OP_VEL1_U1, OP_VEL1_U2, OP_VEL1_U3,
     OP_GRAD_X, OP_GRAD_Y, OP_GRAD_Z, PREC_JACOBI, PREC_IC0, PREC_NONE, PREC_LINE, FP64, FP32_REFINE,
     BF16_REFINE, STEP_LUMPED, STEP_CONSISTENT, SLOT_OFFSETS, NBR_OFFSETS,
     PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_NOT_CONVERGED, PM_BREAKDOWN, PM_TIMEOUT,
-    PM_DISCONNECTED,
+    PM_DISCONNECTED, PM_EBUSY,
 )

@@ -17,7 +17,7 @@ from . import build as _build
 
 # ---- C structures -----------------------------------------------------------------------------
 
-PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_NOT_CONVERGED, PM_BREAKDOWN, PM_TIMEOUT, PM_DISCONNECTED = range(8)
+PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_NOT_CONVERGED, PM_BREAKDOWN, PM_TIMEOUT, PM_DISCONNECTED, PM_EBUSY = range(9)
 PM_WALL_WEST, PM_WALL_EAST, PM_WALL_SOUTH, PM_WALL_NORTH = 1, 2, 4, 8
 OP_VEL_U1, OP_VEL_U2, OP_VEL_U3, OP_PRESSURE, OP_MASS = 0, 1, 2, 3, 4
 OP_VEL1_U1, OP_VEL1_U2, OP_VEL1_U3, OP_GRAD_X, OP_GRAD_Y, OP_GRAD_Z = 5, 6, 7, 8, 9, 10
@@ -94,6 +94,14 @@ SIGNATURES = {
     "pm_batch_destroy": (None, [_P]),
     "pm_pcg_solve_batched": (_I, [_P, _P, _P, _P, ctypes.c_int32, ctypes.POINTER(SolveOpts), _P, _P]),
     "pm_debug_barrier_timeout": (_I, [_P]),
+    "pm_server_create": (_I, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(SolveOpts), ctypes.c_int32,
+                              ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_P), _P]),
+    "pm_server_workspace_bytes": (ctypes.c_size_t, [_P, ctypes.c_int32]),
+    "pm_server_admit": (_I, [_P, _P, _I, _P, _P, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int32), _P]),
+    "pm_server_run": (_I, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _P]),
+    "pm_server_poll": (_I, [_P, _P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "pm_server_info": (_I, [_P, _P, _P, _P, _P, _P]),
+    "pm_server_destroy": (None, [_P]),
     "pm_kernel_timing": (_I, [ctypes.c_int32]),
     "pm_kernel_timing_get": (_I, [ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
 }
@@ -380,6 +388,79 @@ class Batch:
     def close(self):
         if getattr(self, "handle", None):
             load().pm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _handle(h):
+    return h.value if isinstance(h, ctypes.c_void_p) else h
+
+
+class Server:
+    """Continuous batching solve server (pm_server): a slot table advanced by the persistent kernel,
+    systems admitted and retired between launches."""
+
+    def __init__(self, slots: int = 64, nz_cap: int = 64, opts: Options = None, tile_cols: int = 64,
+                 block: int = 128, blocks_per_sm: int = 0, stream=None):
+        opts = opts or Options(prec=PREC_LINE, precision=FP32_REFINE, rtol=1e-8, inner_rtol=1e-2)
+        self.opts = opts
+        self.slots = slots
+        o = opts.c()
+        h = ctypes.c_void_p()
+        _check(load().pm_server_create(slots, nz_cap, ctypes.byref(o), tile_cols, block, blocks_per_sm,
+                                       ctypes.byref(h), _stream(stream)), "server_create")
+        self.handle = h
+        self._out_slots = (ctypes.c_int32 * slots)()
+        self._out_stats = (SolveStats * slots)()
+
+    def workspace_bytes(self, op: Operator) -> int:
+        return int(load().pm_server_workspace_bytes(_handle(op.handle), self.opts.precision))
+
+    def admit(self, op: Operator, which: int, b, x, work, stream=None):
+        """Admit one system; returns its slot, or None when every slot is taken (PM_EBUSY)."""
+        torch = _torch()
+        if not (work.is_cuda and work.dtype == torch.uint8 and work.is_contiguous()):
+            raise ValueError("work must be a contiguous CUDA uint8 tensor")
+        slot = ctypes.c_int32(-1)
+        r = load().pm_server_admit(self.handle, _handle(op.handle), which, _dptr(b, op.n, "b"), _dptr(x, op.n, "x"),
+                                   ctypes.c_void_p(work.data_ptr()), work.numel(), ctypes.byref(slot),
+                                   _stream(stream))
+        if r == PM_EBUSY:
+            return None
+        _check(r, "server_admit")
+        return slot.value
+
+    def run(self, quantum: int = 16, stream=None) -> int:
+        act = ctypes.c_int32(0)
+        _check(load().pm_server_run(self.handle, quantum, ctypes.byref(act), _stream(stream)), "server_run")
+        return act.value
+
+    def poll(self):
+        """Finished systems since the last poll: list of (slot, SolveStats)."""
+        n = ctypes.c_int32(0)
+        _check(load().pm_server_poll(self.handle, self._out_slots, self._out_stats, self.slots, ctypes.byref(n)),
+               "server_poll")
+        out = []
+        for i in range(n.value):
+            out.append((self._out_slots[i], SolveStats.from_buffer_copy(self._out_stats[i])))
+        return out
+
+    def info(self):
+        tc, blk, grid = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        cap, la = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().pm_server_info(self.handle, ctypes.byref(tc), ctypes.byref(blk), ctypes.byref(grid),
+                                     ctypes.byref(cap), ctypes.byref(la)), "server_info")
+        return {"tile_cols": tc.value, "block": blk.value, "grid": grid.value, "tile_capacity": cap.value,
+                "launches": la.value}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().pm_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -98,6 +98,7 @@ const char* pm_status_string(int s) {
     case PM_BREAKDOWN: return "breakdown";
     case PM_TIMEOUT: return "device wait timed out";
     case PM_DISCONNECTED: return "ocean is not connected";
+    case PM_EBUSY: return "no free server slot";
   }
   return "unknown status";
 }

@@ -32,7 +32,11 @@
 namespace pm {
 namespace batch {
 
-enum State : int32_t { ST_ITER = 0, ST_REFINE = 1, ST_RESTART = 2, ST_DONE = 3 };
+// NEW: admitted, not initialised; PINIT: r, z set, p pending; SHIFT / SHIFT2: converged pressure
+// system whose solution is being moved to zero mean (m'x = 0).
+enum State : int32_t {
+  ST_ITER = 0, ST_REFINE = 1, ST_RESTART = 2, ST_DONE = 3, ST_NEW = 4, ST_PINIT = 5, ST_SHIFT = 6, ST_SHIFT2 = 7
+};
 
 struct Sys {
   Geom g;
@@ -60,7 +64,8 @@ struct Tile {
 
 struct Ctl {
   uint32_t bar_count, bar_gen;
-  int32_t err, active;
+  int32_t err, active;   // active: systems not DONE (written by block 0, read at every iteration)
+  int32_t pending, pad;  // pending: NEW systems to initialise at the start of the next launch
 };
 
 constexpr int NP = 4;  // partial lanes per tile
@@ -131,31 +136,39 @@ __device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
 template <typename T>
 __device__ __forceinline__ T ldv(const T* p, int i) { return __ldg(p + i); }
 
-// Row of A (type T, stored as in the single-system paths: FP64 plain, FP32 difference form).
-template <typename T>
-__device__ __forceinline__ double row_apply(const Geom& g, const T* __restrict__ val, const T* x, int maskc,
-                                            int row, int col, int k) {
+// Row of A for phase A. MASKC: velocity component whose Dirichlet rows are identity rows (0, 1, 2;
+// a compile-time constant so the per-slot tests fold), or -1 (pressure: none). The slot values are
+// loaded before the neighbour indices are used, and the iterate with plain loads: this file is
+// compiled with L2-only default loads, and the iterate is written only in other phases.
+template <typename T, int MASKC>
+__device__ __forceinline__ double row_spmv(const Geom& g, const T* __restrict__ val, const T* x, int row, int col,
+                                           int k) {
+  constexpr bool MASK = MASKC >= 0;
   const int nz = g.nz, npad = (int)g.npad;
   int nb[NNBR];
-  uint8_t fl[NNBR];
   nb[0] = col;
 #pragma unroll
   for (int q = 1; q < NNBR; ++q) nb[q] = __ldg(g.nbr + col * NNBR + q);
+  T a[NSLOT];
 #pragma unroll
-  for (int q = 0; q < NNBR; ++q) fl[q] = __ldg(g.colflag + (nb[q] >= 0 ? nb[q] : col));
-  const T xi = ldcg(x + row);
-  if (maskc >= 0 && is_dirichlet(fl[0], k, nz, maskc)) return (double)xi;
+  for (int s = 0; s < NSLOT; ++s) a[s] = __ldg(val + s * npad + row);
+  uint8_t fl[NNBR];
+  if (MASK) {
+#pragma unroll
+    for (int q = 0; q < NNBR; ++q) fl[q] = __ldg(g.colflag + (nb[q] >= 0 ? nb[q] : col));
+  }
+  const T xi = x[row];
+  if (MASK && is_dirichlet(fl[0], k, nz, MASKC)) return (double)xi;
   if constexpr (std::is_same<T, double>::value) {
     double sum = 0.0;
 #pragma unroll
     for (int s = 0; s < NSLOT; ++s) {
       const int q = slot_q(s), kk = k + slot_dk(s);
-      bool ok = nb[q] >= 0;
+      bool ok = nb[q] >= 0;  // geometry only: the load address does not wait for the flags
       if (slot_dk(s) < 0) ok = ok && kk >= 0;
       if (slot_dk(s) > 0) ok = ok && kk < nz;
-      if (maskc >= 0) ok = ok && !is_dirichlet(fl[q], kk, nz, maskc);
-      const double a = ldv(val, s * npad + row);
-      sum = fma(ok ? a : 0.0, ldcg(x + (ok ? nb[q] * nz + kk : row)), sum);
+      const bool keep = MASK ? ok && !is_dirichlet(fl[q], kk, nz, MASKC) : ok;
+      sum = fma(keep ? a[s] : 0.0, x[ok ? nb[q] * nz + kk : row], sum);
     }
     return sum;
   } else {
@@ -168,31 +181,67 @@ __device__ __forceinline__ double row_apply(const Geom& g, const T* __restrict__
       if (slot_dk(s) < 0) ok = ok && kk >= 0;
       if (slot_dk(s) > 0) ok = ok && kk < nz;
       bool keep = ok;
-      const float a = ldv(val, s * npad + row);
-      if (maskc >= 0) {
-        const bool dj = ok && is_dirichlet(fl[q], kk, nz, maskc);
+      if (MASK) {
+        const bool dj = ok && is_dirichlet(fl[q], kk, nz, MASKC);
         keep = ok && !dj;
-        drop += dj ? a : 0.f;
+        drop += dj ? a[s] : 0.f;
       }
-      sum = fmaf(keep ? a : 0.f, ldcg(x + (keep ? nb[q] * nz + kk : row)) - xi, sum);
+      sum = fmaf(keep ? a[s] : 0.f, x[ok ? nb[q] * nz + kk : row] - xi, sum);
     }
-    return (double)fmaf(ldv(val, DIAG_SLOT * npad + row) - drop, xi, sum);
+    return (double)fmaf(a[DIAG_SLOT] - drop, xi, sum);
   }
 }
 
-// FP64 row with |A||x| (true residual and its floor).
+// Phase A of one tile: w = A p on its rows, returns the partial (p, w). Two rows per thread are
+// computed before either is stored.
+template <typename T, int MASKC>
+__device__ __forceinline__ double spmv_tile(const Sys& S, int row0, int rows, int nz) {
+  const T* p = (const T*)S.p;
+  T* w = (T*)S.w;
+  const T* val = (const T*)S.val;
+  const Geom g = S.g;
+  const int bd = blockDim.x;
+  double acc = 0.0;
+  for (int i0 = threadIdx.x; i0 < rows; i0 += 2 * bd) {
+    double wv[2];
+    T pv[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int row = row0 + min(i0 + u * bd, rows - 1), col = row / nz, k = row - col * nz;
+      wv[u] = row_spmv<T, MASKC>(g, val, p, row, col, k);
+      pv[u] = p[row];
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (i0 + u * bd < rows) {
+        w[row0 + i0 + u * bd] = (T)wv[u];
+        acc = fma((double)pv[u], wv[u], acc);
+      }
+    }
+  }
+  return acc;
+}
+
+// FP64 row with |A||x| (true residual and its floor); MASKC as row_spmv.
+template <int MASKC>
 __device__ __forceinline__ double row_apply64_abs(const Geom& g, const double* __restrict__ val, const double* x,
-                                                  int maskc, int row, int col, int k, double& asum) {
+                                                  int row, int col, int k, double& asum) {
+  constexpr bool MASK = MASKC >= 0;
   const int nz = g.nz, npad = (int)g.npad;
   int nb[NNBR];
-  uint8_t fl[NNBR];
   nb[0] = col;
 #pragma unroll
   for (int q = 1; q < NNBR; ++q) nb[q] = __ldg(g.nbr + col * NNBR + q);
+  double a[NSLOT];
 #pragma unroll
-  for (int q = 0; q < NNBR; ++q) fl[q] = __ldg(g.colflag + (nb[q] >= 0 ? nb[q] : col));
-  if (maskc >= 0 && is_dirichlet(fl[0], k, nz, maskc)) {
-    const double xi = ldcg(x + row);
+  for (int s = 0; s < NSLOT; ++s) a[s] = __ldg(val + s * npad + row);
+  uint8_t fl[NNBR];
+  if (MASK) {
+#pragma unroll
+    for (int q = 0; q < NNBR; ++q) fl[q] = __ldg(g.colflag + (nb[q] >= 0 ? nb[q] : col));
+  }
+  const double xi = x[row];
+  if (MASK && is_dirichlet(fl[0], k, nz, MASKC)) {
     asum = fabs(xi);
     return xi;
   }
@@ -204,13 +253,32 @@ __device__ __forceinline__ double row_apply64_abs(const Geom& g, const double* _
     bool ok = nb[q] >= 0;
     if (slot_dk(s) < 0) ok = ok && kk >= 0;
     if (slot_dk(s) > 0) ok = ok && kk < nz;
-    if (maskc >= 0) ok = ok && !is_dirichlet(fl[q], kk, nz, maskc);
-    const double a = ok ? __ldg(val + s * npad + row) : 0.0;
-    const double xv = ldcg(x + (ok ? nb[q] * nz + kk : row));
-    sum = fma(a, xv, sum);
-    asum += fabs(a * xv);
+    const bool keep = MASK ? ok && !is_dirichlet(fl[q], kk, nz, MASKC) : ok;
+    const double av = keep ? a[s] : 0.0;
+    const double xv = x[ok ? nb[q] * nz + kk : row];
+    sum = fma(av, xv, sum);
+    asum += fabs(av * xv);
   }
   return sum;
+}
+
+// Phase A of a REFINE system's tile: r = b' - A x in FP64, partials of (r, r) and of the floor
+// (|A||x| + |b|)^2.
+template <typename T, int MASKC>
+__device__ __forceinline__ void refine_tile(const Sys& S, int row0, int rows, int nz, double& rr, double& ff) {
+  T* r = (T*)S.r;
+  const Geom g = S.g;
+  for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+    const int row = row0 + i, col = row / nz, k = row - col * nz;
+    double asum;
+    const double ax = row_apply64_abs<MASKC>(g, S.val64, S.x, row, col, k, asum);
+    const double bi = S.bw[row];
+    const double ri = bi - ax;
+    r[row] = (T)ri;
+    rr = fma(ri, ri, rr);
+    const double f = asum + fabs(bi);
+    ff = fma(f, f, ff);
+  }
 }
 
 // Per-system reduction of tile partials (lane `lane`, tiles [t0, t0 + nt)), one block.
@@ -223,41 +291,113 @@ __device__ __forceinline__ double sys_reduce(const double* part, int ntiles_tota
 
 // Tiles a block owns (t = blockIdx.x mod gridDim.x) among the systems a phase works on, visited
 // system by system so that finished systems cost nothing. mode 0: ITER or REFINE (phase A),
-// 1: ITER or RESTART (phase B), 2: ITER (phase C).
+// 1: ITER, RESTART or SHIFT (phase B), 2: ITER or SHIFT2 (phase C), 3: NEW, 4: PINIT.
 __device__ __forceinline__ bool phase_active(int state, int mode) {
-  return mode == 0 ? (state == ST_ITER || state == ST_REFINE)
-       : mode == 1 ? (state == ST_ITER || state == ST_RESTART) : state == ST_ITER;
-}
-__device__ __forceinline__ int owned_tile(const Sys* sys, const Scal* scal, int nsys, int s, int mode) {
-  const int G = gridDim.x;
-  for (; s < nsys; ++s) {
-    if (!phase_active(scal[s].state, mode)) continue;
-    const int t0 = sys[s].tile0, te = t0 + sys[s].ntiles;
-    const int t = t0 + (((int)blockIdx.x - t0) % G + G) % G;
-    if (t < te) return t;
+  switch (mode) {
+    case 0: return state == ST_ITER || state == ST_REFINE;
+    case 1: return state == ST_ITER || state == ST_RESTART || state == ST_SHIFT;
+    case 2: return state == ST_ITER || state == ST_SHIFT2;
+    case 3: return state == ST_NEW;
+    default: return state == ST_PINIT;
   }
-  return -1;
 }
-__device__ __forceinline__ int next_owned(const Sys* sys, const Scal* scal, const Tile* tiles, int nsys, int t,
-                                          int mode) {
-  const int s = tiles[t].sys;
-  const int nt = t + gridDim.x;
-  return nt < sys[s].tile0 + sys[s].ntiles ? nt : owned_tile(sys, scal, nsys, s + 1, mode);
+// Vertical-line solve of one column in shared memory (cs[0..nz)), level-major factors F: forward
+// sweep y_k = (c_k - l_k y_{k-1}) d_k, back substitution z_k = y_k - u_k z_{k+1}. The factors are
+// constant during the kernel; they are read CH levels at a time so that CH loads are in flight.
+template <typename T>
+__device__ __forceinline__ void line_sweep(T* cs, const T* __restrict__ F, int col, int nc, int n, int nz) {
+  constexpr int CH = sizeof(T) == 8 ? 4 : 8;
+  T y = 0;
+  for (int k0 = 0; k0 < nz; k0 += CH) {
+    T fl[CH], fd[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int li = min(k0 + u, nz - 1) * nc + col;
+      fl[u] = __ldg(F + li);
+      fd[u] = __ldg(F + n + li);
+    }
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      if (k0 + u < nz) {
+        y = (cs[k0 + u] - fl[u] * y) * fd[u];
+        cs[k0 + u] = y;
+      }
+    }
+  }
+  T zn = y;
+  for (int k0 = nz - 2; k0 >= 0; k0 -= CH) {
+    T fu[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) fu[u] = __ldg(F + 2 * n + max(k0 - u, 0) * nc + col);
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      if (k0 - u >= 0) {
+        zn = cs[k0 - u] - fu[u] * zn;
+        cs[k0 - u] = zn;
+      }
+    }
+  }
 }
+
+// Ordered list (shared memory) of the systems active in a phase, built by every block from the
+// states in one parallel pass; returns its length. Tiles a block owns in a system: t = blockIdx.x
+// mod gridDim.x within the system's range, so which block runs a tile never changes the sums.
+__device__ int phase_list(const Scal* scal, int nsys, int mode, int* list, int* wsum) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int base = 0;
+  for (int s0 = 0; s0 < nsys; s0 += blockDim.x) {
+    const int s = s0 + threadIdx.x;
+    const bool a = s < nsys && phase_active(scal[s].state, mode);
+    const unsigned m = __ballot_sync(0xffffffffu, a);
+    __syncthreads();
+    if (lane == 0) wsum[wid] = __popc(m);
+    __syncthreads();
+    int off = base, tot = base;
+    for (int w = 0; w < nw; ++w) {
+      off += w < wid ? wsum[w] : 0;
+      tot += wsum[w];
+    }
+    if (a) list[off + __popc(m & ((1u << lane) - 1u))] = s;
+    base = tot;
+  }
+  __syncthreads();
+  return base;
+}
+
+__device__ __forceinline__ int first_owned(const Sys* sys, int s) {
+  const int G = gridDim.x, t0 = sys[s].tile0;
+  return t0 + (((int)blockIdx.x - t0) % G + G) % G;
+}
+
+// for (t over the tiles this block owns among the systems active in MODE)
+#define FOR_OWNED_TILES(MODE, t)                                                                    \
+  for (int a_ = 0, na_ = phase_list(scal, nsys, MODE, slist, wsum); a_ < na_; ++a_)                \
+    for (int t = first_owned(sys, slist[a_]), te_ = sys[slist[a_]].tile0 + sys[slist[a_]].ntiles; \
+         t < te_; t += gridDim.x)
+
+// Resident blocks of 256 threads per SM the register budget is sized for (128 registers at 2: no
+// spills; measured faster than 80 registers at 3 for the long pressure solves).
+#ifndef PM_BATCH_MINB
+#define PM_BATCH_MINB 2
+#endif
 
 template <typename T>
-__global__ void __launch_bounds__(256, 4) k_batch(const Sys* __restrict__ sys, Scal* scal, int nsys,
+__global__ void __launch_bounds__(256, PM_BATCH_MINB) k_batch(const Sys* __restrict__ sys, Scal* scal, int nsys,
                                                const Tile* __restrict__ tiles, int ntiles, double* part, Ctl* ctl,
                                                int quantum, int init) {
-  extern __shared__ unsigned char smem_raw[];
-  T* smt = reinterpret_cast<T*>(smem_raw);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int* slist = reinterpret_cast<int*>(smem_raw);                             // nsys entries
+  T* smt = reinterpret_cast<T*>(smem_raw + ((size_t)nsys * 4 + 15) / 16 * 16);  // tile of columns
   __shared__ double red[NP * 32];
+  __shared__ int wsum[32];
   const int tid = threadIdx.x;
 
-  // ---- initialisation: projected right-hand side, r = b' (x = 0), z, p, rho ----------------------
-  if (init) {
+  // ---- initialisation of NEW systems: projected right-hand side, r = b' (x = 0), z, p, rho --------
+  // Runs on the init launch of a batch and, for systems admitted between launches (continuous
+  // batching), at the start of the next launch; systems already iterating wait at the barriers.
+  if (init || *((volatile int32_t*)&ctl->pending) != 0) {
     // I1: tile partials of 1'b (pressure)
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    FOR_OWNED_TILES(3, t) {
       const Tile tl = tiles[t];
       const Sys& S = sys[tl.sys];
       const int nz = S.g.nz, row0 = tl.col0 * nz, rows = tl.ncols * nz;
@@ -270,12 +410,13 @@ __global__ void __launch_bounds__(256, 4) k_batch(const Sys* __restrict__ sys, S
     if (!grid_barrier(ctl)) return;
     for (int s = blockIdx.x; s < nsys; s += gridDim.x) {
       const Sys& S = sys[s];
+      if (scal[s].state != ST_NEW) continue;
       const double sb = sys_reduce(part, ntiles, 0, S.tile0, S.ntiles, red);
       if (tid == 0) scal[s].proj_c = S.proj ? sb / S.one_m : 0.0;  // lambda, reused below
     }
     if (!grid_barrier(ctl)) return;
     // I2: b' = b - lambda m; x = 0; r = b'; z = P^{-1} r (Jacobi / line) and partials
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    FOR_OWNED_TILES(3, t) {
       const Tile tl = tiles[t];
       const Sys& S = sys[tl.sys];
       const int nz = S.g.nz, ld = nz + 1, row0 = tl.col0 * nz, rows = tl.ncols * nz;
@@ -293,23 +434,8 @@ __global__ void __launch_bounds__(256, 4) k_batch(const Sys* __restrict__ sys, S
         if (S.prec == PM_PREC_LINE) smt[(i / nz) * ld + i % nz] = (T)bi;
       }
       __syncthreads();
-      if (S.prec == PM_PREC_LINE && tid < tl.ncols) {
-        const T* F = (const T*)S.lineF;
-        const int col = tl.col0 + tid, nc = S.g.ncols, n = (int)S.g.n;
-        T* cs = smt + tid * ld;
-        T y = 0;
-        for (int k = 0; k < nz; ++k) {
-          const int li = k * nc + col;
-          y = (cs[k] - F[li] * y) * F[n + li];
-          cs[k] = y;
-        }
-        T zn = y;
-        for (int k = nz - 2; k >= 0; --k) {
-          const int li = k * nc + col;
-          zn = cs[k] - F[2 * n + li] * zn;
-          cs[k] = zn;
-        }
-      }
+      if (S.prec == PM_PREC_LINE && tid < tl.ncols)
+        line_sweep<T>(smt + tid * ld, (const T*)S.lineF, tl.col0 + tid, S.g.ncols, (int)S.g.n, nz);
       __syncthreads();
       for (int i = tid; i < rows; i += blockDim.x) {
         const int row = row0 + i;
@@ -330,6 +456,7 @@ __global__ void __launch_bounds__(256, 4) k_batch(const Sys* __restrict__ sys, S
     if (!grid_barrier(ctl)) return;
     for (int s = blockIdx.x; s < nsys; s += gridDim.x) {
       const Sys& S = sys[s];
+      if (scal[s].state != ST_NEW) continue;
       double tot[NP];
       for (int l = 0; l < NP; ++l) tot[l] = sys_reduce(part, ntiles, l, S.tile0, S.ntiles, red);
       if (tid == 0) {
@@ -345,13 +472,13 @@ __global__ void __launch_bounds__(256, 4) k_batch(const Sys* __restrict__ sys, S
         c.iter = 0;
         c.outer = 0;
         c.status = PM_OK;
-        c.state = tot[0] == 0.0 ? ST_DONE : ST_ITER;
+        c.state = tot[0] == 0.0 ? ST_DONE : ST_PINIT;
         c.rel_true = 0.0;
       }
     }
     if (!grid_barrier(ctl)) return;
     // p = z - c
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    FOR_OWNED_TILES(4, t) {
       const Tile tl = tiles[t];
       const Sys& S = sys[tl.sys];
       const int nz = S.g.nz, row0 = tl.col0 * nz, rows = tl.ncols * nz;
@@ -359,39 +486,34 @@ __global__ void __launch_bounds__(256, 4) k_batch(const Sys* __restrict__ sys, S
       for (int i = tid; i < rows; i += blockDim.x) ((T*)S.p)[row0 + i] = ldcg(((const T*)S.z) + row0 + i) - c;
     }
     if (!grid_barrier(ctl)) return;
+    for (int s = blockIdx.x; s < nsys; s += gridDim.x)
+      if (tid == 0 && scal[s].state == ST_PINIT) scal[s].state = ST_ITER;
+    if (blockIdx.x == 0 && tid == 0) ctl->pending = 0;
+    if (!grid_barrier(ctl)) return;
   }
 
   for (int it = 0; it < quantum; ++it) {
     if (*((volatile int32_t*)&ctl->active) == 0) return;
     // ---- A: SpMV + (p, w) | REFINE: FP64 residual --------------------------------------------------
-    for (int t = owned_tile(sys, scal, nsys, 0, 0); t >= 0; t = next_owned(sys, scal, tiles, nsys, t, 0)) {
+    FOR_OWNED_TILES(0, t) {
       const Tile tl = tiles[t];
       const Sys& S = sys[tl.sys];
       const int state = scal[tl.sys].state;
       const int nz = S.g.nz, row0 = tl.col0 * nz, rows = tl.ncols * nz;
       double v[NP] = {0.0, 0.0, 0.0, 0.0};
       if (state == ST_ITER) {
-        const T* p = (const T*)S.p;
-        T* w = (T*)S.w;
-#pragma unroll 2
-        for (int i = tid; i < rows; i += blockDim.x) {
-          const int row = row0 + i, col = row / nz, k = row - col * nz;
-          const double wi = row_apply<T>(S.g, (const T*)S.val, p, S.maskc, row, col, k);
-          w[row] = (T)wi;
-          v[0] = fma((double)ldcg(p + row), wi, v[0]);
+        switch (S.maskc) {
+          case 0: v[0] = spmv_tile<T, 0>(S, row0, rows, nz); break;
+          case 1: v[0] = spmv_tile<T, 1>(S, row0, rows, nz); break;
+          case 2: v[0] = spmv_tile<T, 2>(S, row0, rows, nz); break;
+          default: v[0] = spmv_tile<T, -1>(S, row0, rows, nz); break;
         }
       } else if (state == ST_REFINE) {
-        T* r = (T*)S.r;
-        for (int i = tid; i < rows; i += blockDim.x) {
-          const int row = row0 + i, col = row / nz, k = row - col * nz;
-          double asum;
-          const double ax = row_apply64_abs(S.g, S.val64, S.x, S.maskc, row, col, k, asum);
-          const double bi = S.bw[row];
-          const double ri = bi - ax;
-          r[row] = (T)ri;
-          v[0] = fma(ri, ri, v[0]);
-          const double f = asum + fabs(bi);
-          v[1] = fma(f, f, v[1]);
+        switch (S.maskc) {
+          case 0: refine_tile<T, 0>(S, row0, rows, nz, v[0], v[1]); break;
+          case 1: refine_tile<T, 1>(S, row0, rows, nz, v[0], v[1]); break;
+          case 2: refine_tile<T, 2>(S, row0, rows, nz, v[0], v[1]); break;
+          default: refine_tile<T, -1>(S, row0, rows, nz, v[0], v[1]); break;
         }
       }
       block_sum<2>(*reinterpret_cast<double(*)[2]>(v), red);
@@ -422,10 +544,10 @@ __global__ void __launch_bounds__(256, 4) k_batch(const Sys* __restrict__ sys, S
           c.rel_true = sqrt(a0 / c.bb);
           c.rel_floor = ldexp(1.0, -53) * sqrt(a1 / c.bb);
           if (c.rel_true <= fmax(c.rtol, c.rel_floor)) {
-            c.state = ST_DONE;
+            c.state = S.proj ? ST_SHIFT : ST_DONE;
           } else if (c.iter >= c.max_iter || c.outer > 64) {
             c.status = PM_NOT_CONVERGED;
-            c.state = ST_DONE;
+            c.state = S.proj ? ST_SHIFT : ST_DONE;
           } else {
             c.state = ST_RESTART;
             c.inner_tol2 = std::is_same<T, double>::value ? c.tol2 : c.inner_rtol * c.inner_rtol * a0;
@@ -436,57 +558,82 @@ __global__ void __launch_bounds__(256, 4) k_batch(const Sys* __restrict__ sys, S
     }
     if (!grid_barrier(ctl)) return;
     // ---- B: update + preconditioner + dots | RESTART: preconditioner + dots ---------------------------
-    for (int t = owned_tile(sys, scal, nsys, 0, 1); t >= 0; t = next_owned(sys, scal, tiles, nsys, t, 1)) {
+    FOR_OWNED_TILES(1, t) {
       const Tile tl = tiles[t];
       const Sys& S = sys[tl.sys];
       const int state = scal[tl.sys].state;
       double v[NP] = {0.0, 0.0, 0.0, 0.0};
-      if (state == ST_ITER || state == ST_RESTART) {
+      if (state == ST_SHIFT) {  // partial of m'x for the zero-mean shift
+        const int nz = S.g.nz, row0 = tl.col0 * nz, rows = tl.ncols * nz;
+        for (int i = tid; i < rows; i += blockDim.x) v[0] = fma(S.m[row0 + i], S.x[row0 + i], v[0]);
+      } else if (state == ST_ITER || state == ST_RESTART) {
         const int nz = S.g.nz, ld = nz + 1, row0 = tl.col0 * nz, rows = tl.ncols * nz;
         const double alpha = state == ST_ITER ? scal[tl.sys].alpha : 0.0;
         T* r = (T*)S.r;
         T* z = (T*)S.z;
         const T* p = (const T*)S.p;
         const T* w = (const T*)S.w;
-        for (int i = tid; i < rows; i += blockDim.x) {
-          const int row = row0 + i;
-          T ri = ldcg(r + row);
-          if (state == ST_ITER) {
-            S.x[row] = fma(alpha, (double)ldcg(p + row), S.x[row]);
-            ri = ri - (T)alpha * ldcg(w + row);
-            r[row] = ri;
+        const int bd = blockDim.x;
+        double* xg = S.x;
+        constexpr int U = 4;  // rows i0 + u bd: all loads first, then updates and stores
+        for (int i0 = tid; i0 < rows; i0 += U * bd) {
+          T rv[U], pv[U], wv[U];
+          double xv[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int row = row0 + min(i0 + u * bd, rows - 1);
+            rv[u] = ldcg(r + row);
+            if (state == ST_ITER) {
+              pv[u] = ldcg(p + row);
+              wv[u] = ldcg(w + row);
+              xv[u] = ldcg(xg + row);
+            }
           }
-          v[0] = fma((double)ri, (double)ri, v[0]);
-          if (S.prec == PM_PREC_LINE) smt[(i / nz) * ld + i % nz] = ri;
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * bd;
+            if (i < rows) {
+              const int row = row0 + i;
+              T ri = rv[u];
+              if (state == ST_ITER) {
+                xg[row] = fma(alpha, (double)pv[u], xv[u]);
+                ri = ri - (T)alpha * wv[u];
+                r[row] = ri;
+              }
+              v[0] = fma((double)ri, (double)ri, v[0]);
+              if (S.prec == PM_PREC_LINE) smt[(i / nz) * ld + i % nz] = ri;
+            }
+          }
         }
         __syncthreads();
-        if (S.prec == PM_PREC_LINE && tid < tl.ncols) {
-          const T* F = (const T*)S.lineF;
-          const int col = tl.col0 + tid, nc = S.g.ncols, n = (int)S.g.n;
-          T* cs = smt + tid * ld;
-          T y = 0;
-          for (int k = 0; k < nz; ++k) {
-            const int li = k * nc + col;
-            y = (cs[k] - F[li] * y) * F[n + li];
-            cs[k] = y;
-          }
-          T zn = y;
-          for (int k = nz - 2; k >= 0; --k) {
-            const int li = k * nc + col;
-            zn = cs[k] - F[2 * n + li] * zn;
-            cs[k] = zn;
-          }
-        }
+        if (S.prec == PM_PREC_LINE && tid < tl.ncols)
+          line_sweep<T>(smt + tid * ld, (const T*)S.lineF, tl.col0 + tid, S.g.ncols, (int)S.g.n, nz);
         __syncthreads();
-        for (int i = tid; i < rows; i += blockDim.x) {
-          const int row = row0 + i;
-          const T ri = ldcg(r + row);
-          const T zi = S.prec == PM_PREC_LINE ? smt[(i / nz) * ld + i % nz] : (T)(((const T*)S.dinv)[row] * ri);
-          z[row] = zi;
-          v[1] = fma((double)ri, (double)zi, v[1]);
-          if (S.proj) {
-            v[2] = fma(S.m[row], (double)zi, v[2]);
-            v[3] += (double)ri;
+        const bool line = S.prec == PM_PREC_LINE;
+        const T* dinv = (const T*)S.dinv;
+        for (int i0 = tid; i0 < rows; i0 += U * bd) {
+          T rv[U], dv[U];
+          double mv[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int row = row0 + min(i0 + u * bd, rows - 1);
+            rv[u] = ldcg(r + row);
+            dv[u] = line ? (T)0 : __ldg(dinv + row);
+            mv[u] = S.proj ? __ldg(S.m + row) : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * bd;
+            if (i < rows) {
+              const T ri = rv[u];
+              const T zi = line ? smt[(i / nz) * ld + i % nz] : (T)(dv[u] * ri);
+              z[row0 + i] = zi;
+              v[1] = fma((double)ri, (double)zi, v[1]);
+              if (S.proj) {
+                v[2] = fma(mv[u], (double)zi, v[2]);
+                v[3] += (double)ri;
+              }
+            }
           }
         }
       }
@@ -501,13 +648,16 @@ __global__ void __launch_bounds__(256, 4) k_batch(const Sys* __restrict__ sys, S
       const Sys& S = sys[s];
       Scal& c = scal[s];
       const int state = c.state;
-      if (state != ST_ITER && state != ST_RESTART) continue;
+      if (state != ST_ITER && state != ST_RESTART && state != ST_SHIFT) continue;
       double tot[NP];
       for (int l = 0; l < NP; ++l) tot[l] = sys_reduce(part, ntiles, l, S.tile0, S.ntiles, red);
       if (tid == 0) {
         const double cc = S.proj ? tot[2] / S.one_m : 0.0;
         const double rho_new = tot[1] - cc * tot[3];
-        if (state == ST_RESTART) {
+        if (state == ST_SHIFT) {
+          c.proj_c = tot[0] / S.one_m;  // x -= m'x / 1'm in phase C
+          c.state = ST_SHIFT2;
+        } else if (state == ST_RESTART) {
           c.proj_c = cc;
           c.rho = rho_new;
           c.beta = 0.0;
@@ -537,59 +687,46 @@ __global__ void __launch_bounds__(256, 4) k_batch(const Sys* __restrict__ sys, S
       }
     }
     if (!grid_barrier(ctl)) return;
-    // ---- C: p = (z - c) + beta p; count active systems ------------------------------------------------
-    if (blockIdx.x == 0 && tid == 0) {
+    // ---- C: p = (z - c) + beta p | SHIFT2: x -= shift; count systems still active -----------------------
+    if (blockIdx.x == 0) {
       int act = 0;
-      for (int s = 0; s < nsys; ++s) act += scal[s].state != ST_DONE;
-      ctl->active = act;
+      for (int s0 = 0; s0 < nsys; s0 += blockDim.x) {
+        const int st = s0 + tid < nsys ? scal[s0 + tid].state : (int)ST_DONE;
+        act += __syncthreads_count(st != ST_DONE && st != ST_SHIFT2);
+      }
+      if (tid == 0) ctl->active = act;
     }
-    for (int t = owned_tile(sys, scal, nsys, 0, 2); t >= 0; t = next_owned(sys, scal, tiles, nsys, t, 2)) {
+    FOR_OWNED_TILES(2, t) {
       const Tile tl = tiles[t];
       const Sys& S = sys[tl.sys];
-      if (scal[tl.sys].state != ST_ITER) continue;
       const int nz = S.g.nz, row0 = tl.col0 * nz, rows = tl.ncols * nz;
+      if (scal[tl.sys].state == ST_SHIFT2) {
+        const double sh = scal[tl.sys].proj_c;
+        for (int i = tid; i < rows; i += blockDim.x) S.x[row0 + i] -= sh;
+        continue;
+      }
       const T beta = (T)scal[tl.sys].beta, c = (T)scal[tl.sys].proj_c;
       T* p = (T*)S.p;
       const T* z = (const T*)S.z;
-      for (int i = tid; i < rows; i += blockDim.x) {
-        const int row = row0 + i;
-        p[row] = (ldcg(z + row) - c) + beta * ldcg(p + row);
+      const int bd = blockDim.x;
+      constexpr int U = 4;
+      for (int i0 = tid; i0 < rows; i0 += U * bd) {
+        T zv[U], pv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int row = row0 + min(i0 + u * bd, rows - 1);
+          zv[u] = ldcg(z + row);
+          pv[u] = ldcg(p + row);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (i0 + u * bd < rows) p[row0 + i0 + u * bd] = (zv[u] - c) + beta * pv[u];
       }
     }
     if (!grid_barrier(ctl)) return;
-  }
-}
-
-// Final pressure shift: x -= m'x / 1'm (per system, tiles reduced like everything else).
-__global__ void k_batch_sum_mx(const Sys* sys, const Tile* tiles, int ntiles, double* part) {
-  __shared__ double red[32];
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const Tile tl = tiles[t];
-    const Sys& S = sys[tl.sys];
-    const int nz = S.g.nz, row0 = tl.col0 * nz, rows = tl.ncols * nz;
-    double v[1] = {0.0};
-    if (S.proj)
-      for (int i = threadIdx.x; i < rows; i += blockDim.x) v[0] = fma(S.m[row0 + i], S.x[row0 + i], v[0]);
-    block_sum<1>(v, red);
-    if (threadIdx.x == 0) part[t] = v[0];
-  }
-}
-
-__global__ void k_batch_shift(const Sys* sys, const Tile* tiles, int ntiles, const double* part) {
-  __shared__ double red[32];
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const Tile tl = tiles[t];
-    const Sys& S = sys[tl.sys];
-    if (!S.proj) continue;
-    double v[1] = {0.0};
-    for (int i = threadIdx.x; i < S.ntiles; i += blockDim.x) v[0] += part[S.tile0 + i];
-    block_sum<1>(v, red);
-    __shared__ double shift;
-    if (threadIdx.x == 0) shift = v[0] / S.one_m;
-    __syncthreads();
-    const int nz = S.g.nz, row0 = tl.col0 * nz, rows = tl.ncols * nz;
-    for (int i = threadIdx.x; i < rows; i += blockDim.x) S.x[row0 + i] -= shift;
-    __syncthreads();
+    // SHIFT2 -> DONE; no phase before the next C reads SHIFT2 or DONE as active, so no barrier
+    for (int s = blockIdx.x; s < nsys; s += gridDim.x)
+      if (tid == 0 && scal[s].state == ST_SHIFT2) scal[s].state = ST_DONE;
   }
 }
 
@@ -636,10 +773,13 @@ int max_blocks(int block, size_t smem) {
   return nb;
 }
 
-size_t smem_bytes(const pm_batch* bt) {
-  const size_t es = bt->precision == PM_FP64 ? sizeof(double) : sizeof(float);
-  return (size_t)bt->tile_cols * (bt->nz_max + 1) * es;
+// Dynamic shared memory of k_batch: the active-system list (nsys ints) and one tile of columns.
+size_t kernel_smem(int nsys, int tile_cols, int nz, int precision) {
+  const size_t es = precision == PM_FP64 ? sizeof(double) : sizeof(float);
+  return ((size_t)nsys * 4 + 15) / 16 * 16 + (size_t)tile_cols * (nz + 1) * es;
 }
+
+size_t smem_bytes(const pm_batch* bt) { return kernel_smem(bt->count, bt->tile_cols, bt->nz_max, bt->precision); }
 
 void free_layout(pm_batch* bt) {
   if (bt->graph) cudaGraphExecDestroy(bt->graph);
@@ -713,11 +853,11 @@ int build_layout(pm_batch* bt) {
 }
 
 template <typename T>
-cudaError_t launch(pm_batch* bt, int quantum, int init, cudaStream_t s) {
-  const size_t smem = smem_bytes(bt);
+cudaError_t launch_k(int grid, int block, size_t smem, const Sys* d_sys, Scal* d_scal, int nsys, const Tile* d_tiles,
+                     int ntiles, double* d_part, Ctl* d_ctl, int quantum, int init, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(bt->grid);
-  cfg.blockDim = dim3(bt->block);
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -726,8 +866,36 @@ cudaError_t launch(pm_batch* bt, int quantum, int init, cudaStream_t s) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   count_launch();
-  return cudaLaunchKernelEx(&cfg, k_batch<T>, (const Sys*)bt->d_sys, bt->d_scal, (int)bt->count,
-                            (const Tile*)bt->d_tiles, (int)bt->ntiles, bt->d_part, bt->d_ctl, quantum, init);
+  return cudaLaunchKernelEx(&cfg, k_batch<T>, d_sys, d_scal, nsys, d_tiles, ntiles, d_part, d_ctl, quantum, init);
+}
+
+template <typename T>
+cudaError_t launch(pm_batch* bt, int quantum, int init, cudaStream_t s) {
+  return launch_k<T>(bt->grid, bt->block, smem_bytes(bt), bt->d_sys, bt->d_scal, (int)bt->count, bt->d_tiles,
+                     (int)bt->ntiles, bt->d_part, bt->d_ctl, quantum, init, s);
+}
+
+// Capture one launch (made by `fn` on the capture stream) into an executable graph.
+template <typename F>
+int capture_graph(cudaGraphExec_t* exec, F fn) {
+  if (*exec) cudaGraphExecDestroy(*exec);
+  *exec = nullptr;
+  cudaStream_t cs;
+  int st = cuda_check(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+  if (st) return st;
+  cudaGraph_t g;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    const cudaError_t le = fn(cs);
+    e = cudaStreamEndCapture(cs, &g);
+    if (le != cudaSuccess) e = le;
+  }
+  if (e == cudaSuccess) {
+    e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+  }
+  cudaStreamDestroy(cs);
+  return cuda_check(e, "batched PCG graph capture");
 }
 
 int set_grid(pm_batch* bt) {
@@ -750,8 +918,9 @@ int start(pm_batch* bt, cudaStream_t s) {
     hs[i].rtol = bt->rtol;
     hs[i].inner_rtol = bt->inner_rtol;
     hs[i].max_iter = bt->max_iter;
+    hs[i].state = ST_NEW;
   }
-  Ctl c = {0, 0, 0, bt->count};
+  Ctl c = {0, 0, 0, bt->count, 1, 0};
   int st = cuda_check(cudaMemcpyAsync(bt->d_sys, bt->hsys.data(), bt->count * sizeof(Sys), cudaMemcpyHostToDevice, s), "sys");
   if (!st) st = cuda_check(cudaMemcpyAsync(bt->d_scal, hs.data(), bt->count * sizeof(Scal), cudaMemcpyHostToDevice, s), "scal");
   if (!st) st = cuda_check(cudaMemcpyAsync(bt->d_ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, s), "ctl");
@@ -763,24 +932,10 @@ int start(pm_batch* bt, cudaStream_t s) {
 int run_to_completion(pm_batch* bt, cudaStream_t s, int quantum) {
   // capture one quantum launch in a CUDA graph once, replay it until no system is active
   if (!bt->graph || bt->graph_quantum != quantum) {
-    if (bt->graph) cudaGraphExecDestroy(bt->graph);
-    bt->graph = nullptr;
-    cudaStream_t cs;
-    int st = cuda_check(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+    const int st = capture_graph(&bt->graph, [&](cudaStream_t cs) {
+      return bt->precision == PM_FP64 ? launch<double>(bt, quantum, 0, cs) : launch<float>(bt, quantum, 0, cs);
+    });
     if (st) return st;
-    cudaGraph_t g;
-    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-      const cudaError_t le = bt->precision == PM_FP64 ? launch<double>(bt, quantum, 0, cs) : launch<float>(bt, quantum, 0, cs);
-      e = cudaStreamEndCapture(cs, &g);
-      if (le != cudaSuccess) e = le;
-    }
-    if (e == cudaSuccess) {
-      e = cudaGraphInstantiate(&bt->graph, g, 0);
-      cudaGraphDestroy(g);
-    }
-    cudaStreamDestroy(cs);
-    if (e != cudaSuccess) return cuda_check(e, "batched PCG graph capture");
     bt->graph_quantum = quantum;
   }
   Ctl h;
@@ -799,9 +954,6 @@ int run_to_completion(pm_batch* bt, cudaStream_t s, int quantum) {
 }
 
 int finish(pm_batch* bt, pm_solve_stats* stats, cudaStream_t s, double seconds) {
-  k_batch_sum_mx<<<bt->grid, 256, 0, s>>>(bt->d_sys, bt->d_tiles, (int)bt->ntiles, bt->d_part);
-  k_batch_shift<<<bt->grid, 256, 0, s>>>(bt->d_sys, bt->d_tiles, (int)bt->ntiles, bt->d_part);
-  count_launch(2);
   std::vector<Scal> hs(bt->count);
   int st = cuda_check(cudaMemcpyAsync(hs.data(), bt->d_scal, bt->count * sizeof(Scal), cudaMemcpyDeviceToHost, s), "scal");
   if (!st) st = cuda_check(cudaStreamSynchronize(s), "batched PCG finish");
@@ -909,7 +1061,7 @@ using namespace pm;
 
 extern "C" int pm_batch_create(pm_operator* const* ops, const pm_which* which, int32_t count,
                                const pm_solve_opts* opts, int32_t autotune, pm_batch** out, pm_stream stream) {
-  if (!ops || !which || !opts || !out || count <= 0) return set_error(PM_EINVAL, "bad batch arguments");
+  if (!ops || !which || !opts || !out || count <= 0 || count > 4096) return set_error(PM_EINVAL, "bad batch arguments");
   *out = nullptr;
   if (opts->prec != PM_PREC_JACOBI && opts->prec != PM_PREC_LINE && opts->prec != PM_PREC_NONE)
     return set_error(PM_EINVAL, "batched PCG supports PM_PREC_JACOBI, PM_PREC_LINE and PM_PREC_NONE");
@@ -993,6 +1145,354 @@ extern "C" int pm_pcg_solve_batched(pm_operator* const* ops, const pm_which* whi
   st = pm_batch_solve(bt, b, x, stats, stream);
   pm_batch_destroy(bt);
   return st;
+}
+
+// ================================= continuous batching server ======================================
+// A fixed table of slots, each one system (operator x which) with caller-owned vectors and Krylov
+// workspace. Systems are admitted and retired between launches of the persistent kernel: a new
+// system is initialised at the start of the next launch (state NEW) while the others keep their
+// state; a finished one (DONE) frees its slot and its tile range. The kernel takes the whole slot
+// table (empty slots are DONE and cost nothing) and the tile array's capacity as its partial
+// stride, so the captured graph stays valid until the tile array has to grow.
+
+struct pm_server {
+  int32_t cap = 0, nz_cap = 0;
+  int precision = PM_FP64, prec = PM_PREC_JACOBI;
+  double rtol = 1e-8, inner_rtol = 1e-2;
+  int32_t max_iter = 100000;
+  int tile_cols = 64, block = 128, grid = 0, device = 0;
+  std::vector<pm::batch::Sys> hsys;
+  std::vector<pm_operator*> ops;
+  std::vector<int32_t> which;
+  std::vector<uint8_t> used;
+  std::vector<int64_t> tile0, ntiles;
+  std::vector<pm::batch::Tile> htiles;
+  int64_t tcap = 0;
+  pm::batch::Sys* d_sys = nullptr;
+  pm::batch::Scal* d_scal = nullptr;
+  pm::batch::Tile* d_tiles = nullptr;
+  pm::batch::Ctl* d_ctl = nullptr;
+  double* d_part = nullptr;
+  pm::batch::Scal* h_scal = nullptr;  // pinned mirror, refreshed after every launch
+  pm::batch::Ctl* h_ctl = nullptr;    // pinned: [0] read back, [1] upload staging
+  int32_t pending = 0;
+  cudaGraphExec_t graph = nullptr;
+  int graph_quantum = 0;
+  int64_t graph_tcap = 0;
+  int64_t launches = 0;
+};
+
+namespace pm {
+namespace batch {
+namespace {
+
+size_t server_smem(const pm_server* sv) { return kernel_smem(sv->cap, sv->tile_cols, sv->nz_cap, sv->precision); }
+
+void server_free(pm_server* sv) {
+  if (sv->graph) cudaGraphExecDestroy(sv->graph);
+  cudaFree(sv->d_sys);
+  cudaFree(sv->d_scal);
+  cudaFree(sv->d_tiles);
+  cudaFree(sv->d_ctl);
+  cudaFree(sv->d_part);
+  cudaFreeHost(sv->h_scal);
+  cudaFreeHost(sv->h_ctl);
+}
+
+// Tile array capacity >= want: reallocate tiles and partials (contents of the partials need not
+// survive a launch boundary), re-upload the host tile mirror; the graph is re-captured later.
+int server_grow_tiles(pm_server* sv, int64_t want) {
+  if (want <= sv->tcap) return PM_OK;
+  int64_t nc = std::max<int64_t>(sv->tcap * 2, 1024);
+  while (nc < want) nc *= 2;
+  if (nc > (int64_t)1 << 30) return set_error(PM_ENOMEM, "server tile array too large");
+  Tile* nt = nullptr;
+  double* np = nullptr;
+  int st = cuda_check(cudaMalloc((void**)&nt, nc * sizeof(Tile)), "server tiles");
+  if (!st) st = cuda_check(cudaMalloc((void**)&np, (size_t)NP * nc * sizeof(double)), "server partials");
+  if (st) {
+    cudaFree(nt);
+    return st;
+  }
+  sv->htiles.resize(nc, Tile{0, 0, 0, 0});
+  st = cuda_check(cudaMemcpy(nt, sv->htiles.data(), nc * sizeof(Tile), cudaMemcpyHostToDevice), "server tiles");
+  cudaFree(sv->d_tiles);
+  cudaFree(sv->d_part);
+  sv->d_tiles = nt;
+  sv->d_part = np;
+  sv->tcap = nc;
+  return st;
+}
+
+// First-fit tile range of `need` tiles among the occupied slots' ranges; grows the array if none.
+int server_tile_range(pm_server* sv, int64_t need, int64_t* t0) {
+  std::vector<std::pair<int64_t, int64_t>> occ;
+  for (int i = 0; i < sv->cap; ++i)
+    if (sv->used[i]) occ.push_back({sv->tile0[i], sv->tile0[i] + sv->ntiles[i]});
+  std::sort(occ.begin(), occ.end());
+  int64_t cur = 0;
+  for (auto& r : occ) {
+    if (r.first - cur >= need) break;
+    cur = std::max(cur, r.second);
+  }
+  if (cur + need > sv->tcap) {
+    const int st = server_grow_tiles(sv, cur + need);
+    if (st) return st;
+  }
+  *t0 = cur;
+  return PM_OK;
+}
+
+}  // namespace
+}  // namespace batch
+}  // namespace pm
+
+extern "C" size_t pm_server_workspace_bytes(const pm_operator* op, int32_t precision) {
+  if (!op) return 0;
+  const size_t es = precision == PM_FP64 ? sizeof(double) : sizeof(float);
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  return 4 * up((size_t)op->n * es) + up((size_t)op->n * sizeof(double));
+}
+
+extern "C" int pm_server_create(int32_t slots, int32_t nz_cap, const pm_solve_opts* opts, int32_t tile_cols,
+                                int32_t block, int32_t blocks_per_sm, pm_server** out, pm_stream stream) {
+  using namespace pm::batch;
+  if (!opts || !out || slots <= 0 || slots > 4096 || nz_cap < 2 || nz_cap > 4096)
+    return set_error(PM_EINVAL, "bad server arguments");
+  *out = nullptr;
+  if (opts->prec != PM_PREC_JACOBI && opts->prec != PM_PREC_LINE && opts->prec != PM_PREC_NONE)
+    return set_error(PM_EINVAL, "server supports PM_PREC_JACOBI, PM_PREC_LINE and PM_PREC_NONE");
+  if (opts->precision != PM_FP64 && opts->precision != PM_FP32_REFINE)
+    return set_error(PM_EINVAL, "server supports PM_FP64 and PM_FP32_REFINE");
+  if (!(opts->rtol > 0.0)) return set_error(PM_EINVAL, "rtol must be > 0");
+  if (tile_cols != 16 && tile_cols != 32 && tile_cols != 64) return set_error(PM_EINVAL, "tile_cols must be 16, 32 or 64");
+  if ((block != 128 && block != 256) || tile_cols > block) return set_error(PM_EINVAL, "block must be 128 or 256");
+  if (blocks_per_sm < 0) return set_error(PM_EINVAL, "blocks_per_sm must be >= 0");
+  pm_server* sv = new pm_server();
+  sv->cap = slots;
+  sv->nz_cap = nz_cap;
+  sv->precision = opts->precision;
+  sv->prec = opts->prec == PM_PREC_NONE ? PM_PREC_JACOBI : opts->prec;
+  sv->rtol = opts->rtol;
+  sv->inner_rtol = opts->inner_rtol > 0.0 ? opts->inner_rtol : 1e-2;
+  sv->max_iter = opts->max_iter > 0 ? opts->max_iter : 100000;
+  sv->tile_cols = tile_cols;
+  sv->block = block;
+  cudaGetDevice(&sv->device);
+  sv->hsys.assign(slots, Sys{});
+  sv->ops.assign(slots, nullptr);
+  sv->which.assign(slots, 0);
+  sv->used.assign(slots, 0);
+  sv->tile0.assign(slots, 0);
+  sv->ntiles.assign(slots, 0);
+  const size_t smem = server_smem(sv);
+  int st = smem > 160 * 1024 ? set_error(PM_EINVAL, "tile_cols x (nz_cap + 1) does not fit in shared memory") : PM_OK;
+  if (!st) {
+    cudaFuncSetAttribute(k_batch<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    cudaFuncSetAttribute(k_batch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    const int per_sm = sv->precision == PM_FP64 ? max_blocks<double>(block, smem) : max_blocks<float>(block, smem);
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sv->device);
+    if (per_sm <= 0) st = set_error(PM_EINVAL, "server kernel cannot be resident with this block / tile shape");
+    sv->grid = sms * (blocks_per_sm > 0 ? std::min(per_sm, (int)blocks_per_sm) : per_sm);
+  }
+  if (!st) st = cuda_check(cudaMalloc((void**)&sv->d_sys, slots * sizeof(Sys)), "server sys");
+  if (!st) st = cuda_check(cudaMalloc((void**)&sv->d_scal, slots * sizeof(Scal)), "server scal");
+  if (!st) st = cuda_check(cudaMalloc((void**)&sv->d_ctl, sizeof(Ctl)), "server ctl");
+  if (!st) st = cuda_check(cudaMallocHost((void**)&sv->h_scal, slots * sizeof(Scal)), "server scal mirror");
+  if (!st) st = cuda_check(cudaMallocHost((void**)&sv->h_ctl, 2 * sizeof(Ctl)), "server ctl mirror");
+  if (!st) st = server_grow_tiles(sv, 1024);
+  if (!st) {
+    for (int i = 0; i < slots; ++i) {
+      std::memset(&sv->h_scal[i], 0, sizeof(Scal));
+      sv->h_scal[i].state = ST_DONE;
+    }
+    std::memset(sv->h_ctl, 0, 2 * sizeof(Ctl));
+    cudaStream_t s = (cudaStream_t)stream;
+    st = cuda_check(cudaMemcpyAsync(sv->d_scal, sv->h_scal, slots * sizeof(Scal), cudaMemcpyHostToDevice, s), "scal");
+    if (!st) st = cuda_check(cudaMemcpyAsync(sv->d_sys, sv->hsys.data(), slots * sizeof(Sys), cudaMemcpyHostToDevice, s), "sys");
+    if (!st) st = cuda_check(cudaMemcpyAsync(sv->d_ctl, sv->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, s), "ctl");
+    if (!st) st = cuda_check(cudaStreamSynchronize(s), "server create");
+  }
+  if (st) {
+    server_free(sv);
+    delete sv;
+    return st;
+  }
+  *out = sv;
+  return PM_OK;
+}
+
+extern "C" int pm_server_admit(pm_server* sv, pm_operator* op, pm_which which, const double* b, double* x,
+                               void* work, size_t work_bytes, int32_t* slot, pm_stream stream) {
+  using namespace pm::batch;
+  if (!sv || !op || !b || !x || !work || !slot) return set_error(PM_EINVAL, "null server argument");
+  *slot = -1;
+  if (!which_symmetric((int)which)) return set_error(PM_EINVAL, "server entry with a non-symmetric operator");
+  if (op->nz > sv->nz_cap) return set_error(PM_EINVAL, "operator has more levels than the server's nz_cap");
+  if (work_bytes < pm_server_workspace_bytes(op, sv->precision)) return set_error(PM_EINVAL, "workspace too small");
+  if (((uintptr_t)work & 255) != 0) return set_error(PM_EINVAL, "workspace must be 256-byte aligned");
+  int s_i = -1;
+  for (int i = 0; i < sv->cap; ++i)
+    if (!sv->used[i]) {
+      s_i = i;
+      break;
+    }
+  if (s_i < 0) return set_error(PM_EBUSY, "no free server slot");
+  cudaStream_t s = (cudaStream_t)stream;
+  int st = prepare_for_batch(op, (int)which, sv->prec, sv->precision, s);
+  if (st) return st;
+  const int64_t need = (op->ncols + sv->tile_cols - 1) / sv->tile_cols;
+  int64_t t0 = 0;
+  if ((st = server_tile_range(sv, need, &t0))) return st;
+  for (int64_t t = 0; t < need; ++t) {
+    const int c0 = (int)t * sv->tile_cols;
+    sv->htiles[t0 + t] = Tile{s_i, c0, std::min(sv->tile_cols, op->ncols - c0), 0};
+  }
+  const bool f32 = sv->precision != PM_FP64;
+  const size_t es = f32 ? sizeof(float) : sizeof(double);
+  const int w = (int)which, vs = which_valset(w);
+  char* cur = (char*)work;
+  auto take = [&](size_t bytes) {
+    void* p = cur;
+    cur += (bytes + 255) / 256 * 256;
+    return p;
+  };
+  Sys& S = sv->hsys[s_i];
+  S = Sys{};
+  S.g = geom_of(op);
+  S.val = f32 ? (const void*)op->d_val32[vs] : (const void*)op->d_val[vs];
+  S.val64 = op->d_val[vs];
+  S.dinv = f32 ? (const void*)op->d_dinv32[w] : (const void*)op->d_dinv[w];
+  S.lineF = sv->prec == PM_PREC_LINE ? (f32 ? (const void*)op->d_line32[w] : (const void*)op->d_line[w]) : nullptr;
+  S.m = op->d_m;
+  S.one_m = op->one_m;
+  S.maskc = which_mask(w);
+  S.proj = w == PM_OP_PRESSURE;
+  S.prec = sv->prec;
+  S.r = take(op->n * es);
+  S.p = take(op->n * es);
+  S.w = take(op->n * es);
+  S.z = take(op->n * es);
+  S.bw = (double*)take(op->n * sizeof(double));
+  S.b = b;
+  S.x = x;
+  S.tile0 = (int32_t)t0;
+  S.ntiles = (int32_t)need;
+  Scal c;
+  std::memset(&c, 0, sizeof(c));
+  c.rtol = sv->rtol;
+  c.inner_rtol = sv->inner_rtol;
+  c.max_iter = sv->max_iter;
+  c.state = ST_NEW;
+  st = cuda_check(cudaMemcpyAsync(sv->d_tiles + t0, sv->htiles.data() + t0, need * sizeof(Tile), cudaMemcpyHostToDevice, s), "tiles");
+  if (!st) st = cuda_check(cudaMemcpyAsync(sv->d_sys + s_i, &S, sizeof(Sys), cudaMemcpyHostToDevice, s), "sys");
+  if (!st) st = cuda_check(cudaMemcpyAsync(sv->d_scal + s_i, &c, sizeof(Scal), cudaMemcpyHostToDevice, s), "scal");
+  if (st) return st;
+  sv->h_scal[s_i] = c;
+  sv->used[s_i] = 1;
+  sv->ops[s_i] = op;
+  sv->which[s_i] = (int32_t)which;
+  sv->tile0[s_i] = t0;
+  sv->ntiles[s_i] = need;
+  sv->pending += 1;
+  *slot = s_i;
+  return PM_OK;
+}
+
+extern "C" int pm_server_run(pm_server* sv, int32_t quantum, int32_t* active, pm_stream stream) {
+  using namespace pm::batch;
+  if (!sv || quantum <= 0 || quantum > 4096) return set_error(PM_EINVAL, "bad server run arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  int busy = 0;
+  for (int i = 0; i < sv->cap; ++i) busy += sv->used[i] && sv->h_scal[i].state != ST_DONE;
+  if (busy == 0) {
+    if (active) *active = 0;
+    return PM_OK;
+  }
+  int st = PM_OK;
+  if (sv->pending) {  // active / pending fields only; the barrier words and err stay as they are
+    sv->h_ctl[1].active = busy;
+    sv->h_ctl[1].pending = 1;
+    st = cuda_check(cudaMemcpyAsync(&sv->d_ctl->active, &sv->h_ctl[1].active, 2 * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, s), "ctl");
+    if (st) return st;
+  }
+  if (!sv->graph || sv->graph_quantum != quantum || sv->graph_tcap != sv->tcap) {
+    const size_t smem = server_smem(sv);
+    st = capture_graph(&sv->graph, [&](cudaStream_t cs) {
+      return sv->precision == PM_FP64
+                 ? launch_k<double>(sv->grid, sv->block, smem, sv->d_sys, sv->d_scal, sv->cap, sv->d_tiles,
+                                    (int)sv->tcap, sv->d_part, sv->d_ctl, quantum, 0, cs)
+                 : launch_k<float>(sv->grid, sv->block, smem, sv->d_sys, sv->d_scal, sv->cap, sv->d_tiles,
+                                   (int)sv->tcap, sv->d_part, sv->d_ctl, quantum, 0, cs);
+    });
+    if (st) return st;
+    sv->graph_quantum = quantum;
+    sv->graph_tcap = sv->tcap;
+  }
+  st = cuda_check(cudaGraphLaunch(sv->graph, s), "server graph launch");
+  if (st) return st;
+  count_launch();
+  sv->launches += 1;
+  sv->pending = 0;
+  st = cuda_check(cudaMemcpyAsync(sv->h_scal, sv->d_scal, sv->cap * sizeof(Scal), cudaMemcpyDeviceToHost, s), "scal");
+  if (!st) st = cuda_check(cudaMemcpyAsync(sv->h_ctl, sv->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s), "ctl");
+  if (!st) st = cuda_check(cudaStreamSynchronize(s), "server quantum");
+  if (st) return st;
+  if (sv->h_ctl[0].err) return set_error(sv->h_ctl[0].err, "server: a grid barrier wait expired");
+  busy = 0;
+  for (int i = 0; i < sv->cap; ++i) busy += sv->used[i] && sv->h_scal[i].state != ST_DONE;
+  if (active) *active = busy;
+  return PM_OK;
+}
+
+extern "C" int pm_server_poll(pm_server* sv, int32_t* slots, pm_solve_stats* stats, int32_t max_out, int32_t* n_out) {
+  using namespace pm::batch;
+  if (!sv || !slots || !n_out || max_out < 0) return set_error(PM_EINVAL, "bad server poll arguments");
+  int n = 0;
+  const double es = sv->precision == PM_FP64 ? 8.0 : 4.0;
+  for (int i = 0; i < sv->cap && n < max_out; ++i) {
+    if (!sv->used[i] || sv->h_scal[i].state != ST_DONE) continue;
+    const Scal& c = sv->h_scal[i];
+    slots[n] = i;
+    if (stats) {
+      pm_solve_stats& o = stats[n];
+      std::memset(&o, 0, sizeof(o));
+      o.iters = c.iter;
+      o.outer_iters = c.outer;
+      o.first_pass_iters = c.first_pass;
+      o.status = c.status;
+      o.rel_residual_true = c.rel_true;
+      o.rel_residual_rec = c.bb > 0 ? std::sqrt(c.rr / c.bb) : 0.0;
+      o.rel_residual_floor = c.rel_floor;
+      const double nr = (double)sv->ops[i]->n;
+      o.bytes_moved = c.iter * nr * (15 * es + 11 * es + 8 + 8) + c.outer * nr * (15 * 8 + 24);
+    }
+    sv->used[i] = 0;
+    sv->ops[i] = nullptr;
+    sv->ntiles[i] = 0;
+    ++n;
+  }
+  *n_out = n;
+  return PM_OK;
+}
+
+extern "C" int pm_server_info(const pm_server* sv, int32_t* tile_cols, int32_t* block, int32_t* grid, int64_t* tile_capacity,
+                              int64_t* launches) {
+  if (!sv) return set_error(PM_EINVAL, "null server");
+  if (tile_cols) *tile_cols = sv->tile_cols;
+  if (block) *block = sv->block;
+  if (grid) *grid = sv->grid;
+  if (tile_capacity) *tile_capacity = sv->tcap;
+  if (launches) *launches = sv->launches;
+  return PM_OK;
+}
+
+extern "C" void pm_server_destroy(pm_server* sv) {
+  if (!sv) return;
+  pm::batch::server_free(sv);
+  delete sv;
 }
 
 // Test aid: block 1 leaves without arriving at the barrier, so block 0's bounded wait expires.

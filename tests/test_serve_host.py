@@ -1,0 +1,225 @@
+"""Host logic of continuous-batching serving, on a fake backend with a virtual clock (no GPU):
+admission by free slots and device memory, per-session step order, overlap of arrivals with work
+in flight, session residency, the serial baseline, replica sharding over gloo ranks, and host-side
+failure injection."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1207_0486_gb300.serve import Scheduler, shard
+from workloads import request_stream
+
+
+class Stats:
+    def __init__(self, iters, status=0):
+        self.iters = iters
+        self.status = status
+        self.rel_residual_true = 1e-9
+
+
+class FakeBackend:
+    """Virtual clock. A quantum costs `t_launch + t_row * rows of the active systems`; a system
+    needs iters(key) iterations; a serial solve costs its iterations x (t_iter_serial)."""
+
+    def __init__(self, sessions, slots, total_bytes=1 << 40, t_launch=2e-4, t_row=2e-10, t_iter_serial=4e-5,
+                 fail_at_quantum=None):
+        self.sessions = sessions
+        self.slots = slots
+        self.t = 0.0
+        self.total = total_bytes
+        self.open = {}
+        self.active = {}
+        self.next_slot = 0
+        self.t_launch, self.t_row, self.t_iter_serial = t_launch, t_row, t_iter_serial
+        self.max_active = 0
+        self.quanta = 0
+        self.fail_at = fail_at_quantum
+        self.closed = []
+        self.peak_used = 0
+
+    @staticmethod
+    def iters(key):
+        ri, j = key
+        return 20 + (ri * 7 + j * 13) % 60 + (200 if j == 3 else 0)
+
+    def rows(self, s):
+        return s.side * s.side * s.nz
+
+    def now(self):
+        return self.t
+
+    def sleep(self, s):
+        self.t += max(s, 1e-6)
+
+    def session_bytes(self, s):
+        return self.rows(s) * 600
+
+    def free_bytes(self):
+        return self.total - sum(self.session_bytes(self.sessions[h]) for h in self.open.values())
+
+    def open_session(self, sid, s):
+        h = len(self.open) + 1000 * (1 + len(self.closed))
+        self.open[h] = sid
+        self.peak_used = max(self.peak_used, self.total - self.free_bytes())
+        self.t += 1e-4
+        return h
+
+    def close_session(self, h):
+        self.closed.append(self.open.pop(h))
+
+    def admit(self, h, j, seed, key):
+        if len(self.active) >= self.slots:
+            return None
+        free = [s for s in range(self.slots) if s not in self.active]
+        s = free[0]
+        self.active[s] = [key, self.iters(key), self.rows(self.sessions[self.open[h]])]
+        self.max_active = max(self.max_active, len(self.active))
+        return s
+
+    def run(self, quantum):
+        self.quanta += 1
+        if self.fail_at is not None and self.quanta >= self.fail_at:
+            from paper_1207_0486_gb300.api import PMError, PM_TIMEOUT
+            raise PMError(PM_TIMEOUT, "server_run: device wait timed out (injected)")
+        rows = sum(v[2] for v in self.active.values() if v[1] > 0)
+        self.t += self.t_launch + self.t_row * rows * quantum
+        for v in self.active.values():
+            v[1] = max(0, v[1] - quantum)
+        return sum(1 for v in self.active.values() if v[1] > 0)
+
+    def poll(self):
+        out = [(s, Stats(self.iters(v[0]))) for s, v in self.active.items() if v[1] == 0]
+        for s, _ in out:
+            del self.active[s]
+        return out
+
+    def solve_now(self, h, j, seed, key):
+        it = self.iters(key)
+        self.t += it * self.t_iter_serial
+        return Stats(it)
+
+
+def stream(n=300, rate=200.0, sessions=8, steps=20, seed=5):
+    return request_stream(seed=seed, rate=rate, n_requests=n, concurrent_sessions=sessions, steps_per_session=steps,
+                          median_nodes=2e4, sigma=0.8, max_nodes=2e5)
+
+
+def test_all_requests_complete_in_session_order_within_slots():
+    sess, reqs = stream()
+    be = FakeBackend(sess, slots=16)
+    rep = Scheduler(be, sess, reqs, slots=16, quantum=8).run()
+    assert all(not math.isnan(r.t_done) for r in rep.records)
+    assert be.max_active <= 16
+    by_session = {}
+    for r in rep.records:
+        by_session.setdefault(r.session, []).append(r)
+    for rs in by_session.values():
+        rs.sort(key=lambda r: r.step)
+        assert [r.step for r in rs] == list(range(len(rs)))
+        for a, b in zip(rs, rs[1:]):
+            assert a.t_done <= b.t_admit  # step k+1 starts after step k finished
+    # every session closed after its last step; iterations recorded per right-hand side
+    assert sorted(be.closed) == sorted(by_session)
+    assert all(len(r.iters) == r.nrhs and all(i == FakeBackend.iters((r.index, j)) for j, i in enumerate(r.iters))
+               for r in rep.records)
+    s = rep.summary()
+    assert s["solves"] == sum(r.nrhs for r in reqs)
+    assert s["p50_ms"] <= s["p99_ms"] <= s["max_ms"]
+
+
+def test_arrivals_join_while_others_are_in_flight():
+    """Continuous batching: a request is admitted while an earlier-admitted one is still running."""
+    sess, reqs = stream(n=120)
+    rep = Scheduler(FakeBackend(sess, slots=32), sess, reqs, slots=32, quantum=8).run()
+    recs = sorted(rep.records, key=lambda r: r.t_admit)
+    overlaps = sum(1 for a, b in zip(recs, recs[1:]) if b.t_admit < a.t_done)
+    assert overlaps >= len(recs) // 4
+    assert rep.summary()["quanta"] > 0
+
+
+def test_admission_waits_for_device_memory():
+    sess, reqs = stream(n=200, sessions=8, steps=10)
+    rows = [s.side * s.side * s.nz for s in sess]
+    cap = sorted(rows)[-1] * 600 * 2 + (1 << 20)  # room for about two of the largest sessions
+    be = FakeBackend(sess, slots=32, total_bytes=cap)
+    rep = Scheduler(be, sess, reqs, slots=32, quantum=8, reserve_bytes=0).run()
+    assert all(not math.isnan(r.t_done) for r in rep.records)
+    assert be.peak_used <= cap
+    assert rep.deferred_for_memory > 0
+    assert rep.peak_resident_sessions < 8
+
+
+def test_too_few_slots_for_a_request_is_reported():
+    sess, reqs = stream(n=20)
+    big = max(r.nrhs for r in reqs)
+    with pytest.raises(RuntimeError):
+        Scheduler(FakeBackend(sess, slots=big - 1), sess, reqs, slots=big - 1, quantum=8).run()
+
+
+def test_continuous_beats_serial_on_a_batching_backend():
+    sess, reqs = stream(n=300)
+    cont = Scheduler(FakeBackend(sess, slots=64), sess, reqs, slots=64, quantum=8).run().summary()
+    ser = Scheduler(FakeBackend(sess, slots=64), sess, reqs, slots=64, mode="serial").run().summary()
+    assert ser["solves"] == cont["solves"]
+    assert cont["p99_ms"] < ser["p99_ms"]
+    assert cont["solves_per_s"] >= ser["solves_per_s"]
+
+
+def test_injected_device_timeout_propagates():
+    from paper_1207_0486_gb300.api import PMError, PM_TIMEOUT
+    sess, reqs = stream(n=40)
+    with pytest.raises(PMError) as ei:
+        Scheduler(FakeBackend(sess, slots=16, fail_at_quantum=5), sess, reqs, slots=16, quantum=8).run()
+    assert ei.value.status == PM_TIMEOUT
+
+
+def test_shard_partitions_sessions():
+    sess, reqs = stream(n=200)
+    parts = [set(shard(sess, reqs, r, 3)) for r in range(3)]
+    assert set().union(*parts) == set(range(len(reqs)))
+    assert sum(len(p) for p in parts) == len(reqs)
+    for p in parts:
+        assert len({reqs[i].session % 3 for i in p}) <= 1
+
+
+def _replica_rank(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import torch
+    sess, reqs = stream(n=160)
+    mine = shard(sess, reqs, rank, world)
+    sub = [reqs[i] for i in mine]
+    rep = Scheduler(FakeBackend(sess, slots=32), sess, sub, slots=32, quantum=8).run()
+    done = torch.zeros(len(reqs), dtype=torch.int64)
+    for i, r in zip(mine, rep.records):
+        done[i] += 0 if math.isnan(r.t_done) else 1
+    dist.all_reduce(done)
+    span = torch.tensor([rep.makespan], dtype=torch.float64)
+    dist.all_reduce(span, op=dist.ReduceOp.MAX)
+    if rank == 0:
+        q.put((done.tolist(), float(span.item()), rep.makespan))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_replicas_over_gloo_cover_every_request_once():
+    import multiprocessing as mp
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    ps = [ctx.Process(target=_replica_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    done, span_max, span0 = q.get(timeout=120)
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert done == [1] * len(done)
+    assert span_max >= span0

@@ -11,6 +11,8 @@ from .basins import (  # noqa: F401
     ocean_basin,
     batch_basins,
     request_stream,
+    Session,
+    Request,
     mms_modes,
     random_vector,
 )
