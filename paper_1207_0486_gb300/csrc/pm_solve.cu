@@ -585,8 +585,15 @@ __global__ void __launch_bounds__(LINE_TPB) k_line_rho(Geom g, const double* __r
 //   (r, r), (r, z) [m'z, 1'r]. The last block tests convergence on (r, r) and forms beta, as
 //   k_cg_update + k_line_rho would; the z of the converged iteration is simply not used.
 constexpr int LINE_UCOLS = 128;   // FP32 fused kernel: columns (= threads) per block
-constexpr int LINE_FCOLS = 64;    // FP64 fused kernel: columns per block (128 threads stage them)
+#ifndef PM_LINE_FCOLS
+#define PM_LINE_FCOLS 64
+#endif
+#ifndef PM_LINE_UNROLL
+#define PM_LINE_UNROLL 8
+#endif
+constexpr int LINE_FCOLS = PM_LINE_FCOLS;  // FP64 fused kernel: columns per block (128 threads stage them)
 constexpr int LINE_FTPB = 128;
+constexpr int LINE_UNROLL = PM_LINE_UNROLL;  // levels of Thomas factors in flight per sweep thread
 
 // NZ > 0: compile-time column height (shifts instead of divisions); NZ == 0: g.nz at run time.
 template <int PROJ, int NZ>
@@ -621,14 +628,14 @@ __global__ void __launch_bounds__(LINE_FTPB) k_update_line(Geom g, const double*
       const int col = c0 + threadIdx.x;
       double* col_s = smem + threadIdx.x * ld;
       double y = 0.0;
-#pragma unroll 4
+#pragma unroll (LINE_UNROLL)
       for (int k = 0; k < nz; ++k) {
         const int li = k * ncols + col;
         y = (col_s[k] - F[li] * y) * F[n + li];
         col_s[k] = y;
       }
       double zn = y;
-#pragma unroll 4
+#pragma unroll (LINE_UNROLL)
       for (int k = nz - 2; k >= 0; --k) {
         const int li = k * ncols + col;
         zn = fma(-F[2 * n + li], zn, col_s[k]);
