@@ -169,6 +169,28 @@ def run_cpu_oracle(steps: int, warmup: int):
 
 # ---- our arm -----------------------------------------------------------------------------------
 
+def dram_traffic(kernel: str):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of `kernel` from the
+    ncu summary in profiles/traffic.md, or None when the source file the counters were taken on
+    has changed since (its sha256 prefix is recorded next to the figure)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        for line in fh:
+            cells = [c.strip() for c in line.strip().strip("|").split("|")]
+            if len(cells) >= 4 and cells[0] == f"`{kernel}`":
+                src = os.path.join(ROOT, "paper_1207_0486_gb300", "csrc", cells[2])
+                try:
+                    with open(src, "rb") as sf:
+                        digest = hashlib.sha256(sf.read()).hexdigest()[:12]
+                    return int(cells[1]) if digest == cells[3] else None
+                except (OSError, ValueError):
+                    return None
+    return None
+
+
 def _gather_max(dist, v):
     import torch
     if not dist:
@@ -360,25 +382,24 @@ def run_ours(args):
         api.KT_LINE: n * (2 * 8 + 2 * 8 + 8 + 8 + 3 * 8 + 8 + 8 + 8),
     }
     names = {api.KT_SPMV: "k_cg_spmv", api.KT_UPDATE: "k_cg_update", api.KT_PUPDATE: "k_cg_rho+k_cg_pupd",
-             api.KT_IC0: "k_ic0_sweep", api.KT_LINE: "k_line_rho"}
+             api.KT_IC0: "k_ic0_sweep", api.KT_LINE: "k_update_line"}
     dom = max(kt, key=lambda k: kt[k][0])
     dom_ms, dom_launches = kt[dom]
     peak, peak_kind = measured_peaks()
     avg_s = dom_ms * 1e-3 / max(dom_launches, 1)
     achieved = per_launch_bytes[dom] / avg_s / 1e9
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof):
-        try:
-            with open(prof) as fh:
-                traffic = json.load(fh).get(names[dom])
-        except Exception:
-            traffic = None
+    traffic = dram_traffic(names[dom])
     roofline = {"bound": "hbm", "kernel": names[dom], "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": peak_kind,
                 "kernel_share_of_step": round(dom_ms / max(ms_total, 1e-9), 4),
-                "classes_ms_per_step": {names[k]: round(v[0] / args.steps, 3) for k, v in kt.items()}}
+                "classes_ms_per_step": {names[k]: round(v[0] / args.steps, 3) for k, v in kt.items()},
+                "classes": {names[k]: {"launches_per_step": v[1] // max(args.steps, 1),
+                                       "us_per_launch": round(v[0] * 1e3 / max(v[1], 1), 1),
+                                       "gbs": round(per_launch_bytes[k] / (v[0] * 1e-3 / max(v[1], 1)) / 1e9, 1),
+                                       "frac": round(per_launch_bytes[k] / (v[0] * 1e-3 / max(v[1], 1)) / 1e9 / peak,
+                                                     4)}
+                            for k, v in kt.items() if v[1] > 0}}
 
     # end to end through the C ABI with host buffers: theta in, (u1, u2, u3, p) out each step
     e2e = None
