@@ -30,6 +30,7 @@ namespace pm {
 
 struct SolveCtx {
   int64_t n = 0;
+  int line_slots = 0, line_slots_nz = -1;  // resident blocks of the fused line kernel (per nz)
   double *r = nullptr, *p = nullptr, *w = nullptr, *z = nullptr, *bw = nullptr;
   double* partials = nullptr;
   PcgScalars* sc = nullptr;
@@ -601,7 +602,7 @@ __global__ void __launch_bounds__(LINE_FTPB) k_update_line(Geom g, const double*
                                                          double* __restrict__ x, double* __restrict__ r,
                                                          const double* __restrict__ p, const double* __restrict__ w,
                                                          double* __restrict__ z, const double* __restrict__ m,
-                                                         double* partials, PcgScalars* sc) {
+                                                         double* partials, PcgScalars* sc, int nfull_max) {
   extern __shared__ double smem[];
   if (sc_done(sc)) return;
   const double alpha = sc->alpha;
@@ -610,9 +611,14 @@ __global__ void __launch_bounds__(LINE_FTPB) k_update_line(Geom g, const double*
   const int n = (int)g.n;
   const int ntiles = (ncols + LINE_FCOLS - 1) / LINE_FCOLS;
   double v[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int c0 = tile * LINE_FCOLS;
-    const int cc = min(LINE_FCOLS, ncols - c0);
+  // Tiles 0 .. nfull-1 are LINE_FCOLS columns wide (one per resident block: the first wave); the
+  // columns left after them go in half-width tiles, so the second wave is short.
+  const int nfull = min(ntiles, nfull_max);
+  const int rest0 = nfull * LINE_FCOLS;
+  const int nhalf = rest0 < ncols ? (ncols - rest0 + LINE_FCOLS / 2 - 1) / (LINE_FCOLS / 2) : 0;
+  for (int tile = blockIdx.x; tile < nfull + nhalf; tile += gridDim.x) {
+    const int c0 = tile < nfull ? tile * LINE_FCOLS : rest0 + (tile - nfull) * (LINE_FCOLS / 2);
+    const int cc = min(tile < nfull ? LINE_FCOLS : LINE_FCOLS / 2, ncols - c0);
     const int row0 = c0 * nz;
     const int rows = cc * nz;
     for (int i = threadIdx.x; i < rows; i += blockDim.x) {
@@ -681,9 +687,6 @@ __global__ void __launch_bounds__(LINE_FTPB) k_update_line(Geom g, const double*
 void update_line(pm_operator* op, int which, bool proj, double* x, cudaStream_t s) {
   SolveCtx* c = op->ctx;
   Geom g = geom_of(op);
-  const int64_t ntiles = (op->ncols + LINE_FCOLS - 1) / LINE_FCOLS;
-  int grid = (int)std::min<int64_t>(ntiles, std::min<int64_t>((int64_t)op->num_sms * 16, MAX_GRID));
-  if (grid < 1) grid = 1;
   const size_t smem = (size_t)LINE_FCOLS * (op->nz + 1) * sizeof(double);
   static bool attr_set = false;
   if (!attr_set) {
@@ -691,9 +694,25 @@ void update_line(pm_operator* op, int which, bool proj, double* x, cudaStream_t 
     cudaFuncSetAttribute(k_update_line<1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
+  // resident blocks of this shape: the full-width tiles fill exactly one wave of them
+  if (c->line_slots_nz != op->nz) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_line<1, 0>, LINE_FTPB, smem);
+    c->line_slots = std::max(1, per_sm) * op->num_sms;
+    c->line_slots_nz = op->nz;
+  }
+  // four partial lanes per block must fit the partials buffer (NPART x MAX_GRID doubles)
+  const int nfull_max = (int)std::min<int64_t>(c->line_slots, (int64_t)NPART * MAX_GRID / 4);
+  const int64_t nt_full = (op->ncols + LINE_FCOLS - 1) / LINE_FCOLS;
+  const int64_t nfull = std::min<int64_t>(nt_full, nfull_max);
+  const int64_t rest = std::max<int64_t>(0, op->ncols - nfull * LINE_FCOLS);
+  const int64_t ntiles = nfull + (rest + LINE_FCOLS / 2 - 1) / (LINE_FCOLS / 2);
+  int grid = (int)std::min<int64_t>(ntiles, nfull_max);
+  if (grid < 1) grid = 1;
   const double* F = op->d_line[which];
-#define PM_UL(P, NZ) \
-  k_update_line<P, NZ><<<grid, LINE_FTPB, smem, s>>>(g, F, x, c->r, c->p, c->w, c->z, op->d_m, c->partials, c->sc)
+#define PM_UL(P, NZ)                                                                                     \
+  k_update_line<P, NZ><<<grid, LINE_FTPB, smem, s>>>(g, F, x, c->r, c->p, c->w, c->z, op->d_m, c->partials, c->sc, \
+                                                     nfull_max)
   if (op->nz == 32) {
     if (proj) PM_UL(1, 32);
     else PM_UL(0, 32);
