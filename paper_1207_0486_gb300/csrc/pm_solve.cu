@@ -47,9 +47,9 @@ struct ColourMap;  // pm_assemble.cu
 namespace pm {
 
 // ---- live kernel timing (CUDA events on the launching stream) ------------------------------------
-// When enabled, the PCG driver brackets each launch of the timed kernel classes with a pair of
-// events on the solve's stream; elapsed times are collected at the driver's own synchronisation
-// points. Process-global, not thread-safe: enable it from one host thread only.
+// When enabled, the host PCG loop brackets each launch of the timed kernel classes with a pair of
+// events on the solve's stream; elapsed times are collected where that loop synchronises anyway.
+// Process-global, not thread-safe: enable it from one host thread only.
 struct KernelTimer {
   bool on = false;
   std::vector<cudaEvent_t> pool;
