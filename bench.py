@@ -191,22 +191,24 @@ def dram_traffic(kernel: str):
     return None
 
 
-def _gather_max(dist, v):
+def _reduce(dist, v, op):
+    """All-reduce one number over the replicas (NCCL on GPUs, gloo on CPU); v itself without
+    a process group."""
     import torch
     if not dist:
         return v
-    t = torch.tensor([float(v)], device="cuda", dtype=torch.float64)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(v)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def _gather_max(dist, v):
+    return _reduce(dist, v, dist.ReduceOp.MAX) if dist else v
 
 
 def _gather_sum(dist, v):
-    import torch
-    if not dist:
-        return v
-    t = torch.tensor([float(v)], device="cuda", dtype=torch.float64)
-    dist.all_reduce(t)
-    return float(t.item())
+    return _reduce(dist, v, dist.ReduceOp.SUM) if dist else v
 
 
 def run_batched_leg(dist, world, rank):

@@ -125,7 +125,9 @@ class Scheduler:
         slot_of: Dict[int, tuple] = {}     # slot -> (request, j)
         remaining: Dict[int, int] = {}     # request -> systems not finished
         done = 0
-        opened = peak = quanta = deferred = 0
+        opened = peak = quanta = 0
+        deferred = set()                   # requests that waited for device memory at least once
+        need_of: Dict[int, int] = {}       # session -> device bytes it needs when opened
         t0 = be.now()
         first_arrival = recs[order[0]].t_arrival if recs else 0.0
 
@@ -139,12 +141,13 @@ class Scheduler:
                 be.close_session(open_h.pop(rec.session))
 
         def ensure_open(rec) -> bool:
-            nonlocal opened, peak, deferred
+            nonlocal opened, peak
             if rec.session in open_h:
                 return True
-            need = be.session_bytes(self.sessions[rec.session])
-            if be.free_bytes() - need < self.reserve:
-                deferred += 1
+            if rec.session not in need_of:
+                need_of[rec.session] = be.session_bytes(self.sessions[rec.session])
+            if be.free_bytes() - need_of[rec.session] < self.reserve:
+                deferred.add(rec.index)
                 return False
             open_h[rec.session] = be.open_session(rec.session, self.sessions[rec.session])
             opened += 1
@@ -218,7 +221,7 @@ class Scheduler:
                 raise RuntimeError("queued requests can never be admitted (slots or memory too small)")
         last = max((r.t_done for r in recs), default=0.0)
         host = dict(getattr(be, "timers", {}))
-        return ServeReport(self.mode, recs, last - first_arrival, opened, peak, quanta, deferred, host)
+        return ServeReport(self.mode, recs, last - first_arrival, opened, peak, quanta, len(deferred), host)
 
 
 def shard(sessions: Sequence, requests: Sequence, rank: int, world: int):
