@@ -19,10 +19,10 @@
  *     ncols for per-column surface fields) in that node order. The library never frees them.
  *   - Streams: all GPU work of a call is enqueued on the given stream (a cudaStream_t; NULL =
  *     legacy default stream). Calls that report convergence (pm_pcg_solve, pm_project_step,
- *     pm_pcg_solve_batched) synchronise that stream before returning; pm_spmv and the
- *     kernels-only calls are asynchronous.
- *   - Handles (pm_operator, pm_state, pm_batch) are owned by the library and released by their
- *     destroy call. One handle must not be used from two host threads at once; different
+ *     pm_pcg_solve_batched, pm_batch_solve, pm_server_run) synchronise that stream before
+ *     returning; pm_spmv and the kernels-only calls are asynchronous.
+ *   - Handles (pm_operator, pm_state, pm_batch, pm_server) are owned by the library and released
+ *     by their destroy call. One handle must not be used from two host threads at once; different
  *     handles may be.
  */
 #ifndef PM_GB300_H

@@ -13,7 +13,10 @@
 // Per-system reductions sum the tile partials of that system in tile order (deterministic).
 // A system whose recursive residual meets its target moves to REFINE: the FP64 true residual is
 // computed; it is DONE when that meets rtol (or the FP64 floor), otherwise it restarts from the
-// true residual (x is always FP64; with FP32 values this is iterative refinement).
+// true residual (x is always FP64; with FP32 values this is iterative refinement). A pressure
+// system passes through SHIFT (partials of m'x in B) and SHIFT2 (x -= m'x / 1'm in C) on its way
+// to DONE. Systems admitted between launches (NEW) are initialised at the start of the next
+// launch while the others wait at its barriers.
 // The grid barrier spins a bounded number of times; on expiry the kernel records PM_TIMEOUT and
 // every block leaves at its next barrier. Vectors that other blocks write during the kernel are
 // read with ld.global.cg (L2), never through the non-coherent L1.
