@@ -223,3 +223,31 @@ def test_replicas_over_gloo_cover_every_request_once():
         assert p.exitcode == 0
     assert done == [1] * len(done)
     assert span_max >= span0
+
+
+def test_empty_stream():
+    sess, _ = stream(n=10)
+    rep = Scheduler(FakeBackend(sess, slots=8), sess, [], slots=8).run()
+    s = rep.summary()
+    assert s["requests"] == 0 and s["solves"] == 0 and s["p99_ms"] is None
+
+
+@pytest.mark.parametrize("mode", ["continuous", "serial"])
+def test_memory_too_small_for_any_session_is_reported(mode):
+    sess, reqs = stream(n=20)
+    be = FakeBackend(sess, slots=16, total_bytes=1024)
+    with pytest.raises(RuntimeError):
+        Scheduler(be, sess, reqs, slots=16, quantum=8, reserve_bytes=0, mode=mode).run()
+
+
+def test_a_request_needing_every_slot_is_served():
+    from workloads.basins import Request, Session
+    sess = [Session(side=8, nz=8, seed=1), Session(side=10, nz=8, seed=2)]
+    reqs = [Request(t_arrival=0.001 * k, session=k % 2, step=k // 2, nrhs=4, rhs_seed=k) for k in range(6)]
+    be = FakeBackend(sess, slots=4)
+    rep = Scheduler(be, sess, reqs, slots=4, quantum=8).run()
+    assert all(not math.isnan(r.t_done) for r in rep.records)
+    assert be.max_active == 4
+    # with four slots and four right-hand sides per request, requests never overlap
+    recs = sorted(rep.records, key=lambda r: r.t_admit)
+    assert all(b.t_admit >= a.t_done for a, b in zip(recs, recs[1:]))
