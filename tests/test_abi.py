@@ -83,3 +83,45 @@ def test_operator_bytes_scales(lib_path):
     b1 = api.operator_bytes(box_basin(nh=16, nz=8))
     b2 = api.operator_bytes(box_basin(nh=32, nz=8))
     assert b1 > 0 and 3.5 < b2 / b1 < 4.5
+
+
+def test_server_and_batch_validation_without_gpu(lib_path):
+    """The batch and server entry points reject bad arguments on the host, before any CUDA call."""
+    import ctypes
+
+    import paper_1207_0486_gb300.api as api
+    lib = api.load()
+    out = ctypes.c_void_p()
+
+    def opts(**kw):
+        return ctypes.byref(api.Options(**{"rtol": 1e-8, "prec": api.PREC_LINE, **kw}).c())
+
+    good = dict(slots=8, nz_cap=32, tile_cols=64, block=128, bps=0)
+    bad = [dict(slots=0), dict(slots=5000), dict(nz_cap=1), dict(tile_cols=48), dict(tile_cols=16, block=512),
+           dict(bps=-1)]
+    for b in bad:
+        a = {**good, **b}
+        assert lib.pm_server_create(a["slots"], a["nz_cap"], opts(), a["tile_cols"], a["block"], a["bps"],
+                                    ctypes.byref(out), None) == api.PM_EINVAL, b
+    for o in (opts(prec=api.PREC_IC0), opts(precision=api.BF16_REFINE), opts(rtol=0.0)):
+        assert lib.pm_server_create(8, 32, o, 64, 128, 0, ctypes.byref(out), None) == api.PM_EINVAL
+    assert lib.pm_server_create(8, 32, None, 64, 128, 0, ctypes.byref(out), None) == api.PM_EINVAL
+    assert lib.pm_server_workspace_bytes(None, api.FP64) == 0
+    slot = ctypes.c_int32()
+    assert lib.pm_server_admit(None, None, 0, None, None, None, 0, ctypes.byref(slot), None) == api.PM_EINVAL
+    act = ctypes.c_int32()
+    assert lib.pm_server_run(None, 16, ctypes.byref(act), None) == api.PM_EINVAL
+    n = ctypes.c_int32()
+    assert lib.pm_server_poll(None, None, None, 0, ctypes.byref(n)) == api.PM_EINVAL
+    assert lib.pm_server_info(None, None, None, None, None, None) == api.PM_EINVAL
+    lib.pm_server_destroy(None)
+    assert lib.pm_status_string(api.PM_EBUSY).decode() == "no free server slot"
+
+    ops = (ctypes.c_void_p * 2)(None, None)
+    which = (ctypes.c_int * 2)(0, 3)
+    for count, o in ((0, opts()), (5000, opts()), (2, opts(prec=api.PREC_IC0)), (2, opts(precision=api.BF16_REFINE)),
+                     (2, opts(rtol=-1.0))):
+        assert lib.pm_batch_create(ops, which, count, o, 0, ctypes.byref(out), None) == api.PM_EINVAL
+    assert lib.pm_batch_solve(None, None, None, None, None) == api.PM_EINVAL
+    assert lib.pm_batch_info(None, None, None, None, None) == api.PM_EINVAL
+    lib.pm_batch_destroy(None)
