@@ -11,7 +11,8 @@ served by one loop:
     a session's operators, vectors and workspace stay resident across its consecutive steps and
     are released after its last one.
 Right-hand side j of a request is the system of the projection step it stands for: the three
-velocity components (j = 0, 1, 2; Eq. 10) and the pressure increment (j = 3; Eq. 11).
+velocity components (j = 0, 1, 2; Eq. fofa_velo_pred_h) and the pressure increment (j = 3;
+Eq. fofa_q_cor_h).
 
 The loop talks to a backend (the GPU one below, or a host fake in tests), so the scheduling logic
 is the same code whichever runs the solves. `serial` mode is the plain baseline: requests in
