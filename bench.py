@@ -195,6 +195,58 @@ def run_cpu_oracle_all_cores(max_workers: int = 16):
 
 # ---- our arm -----------------------------------------------------------------------------------
 
+# live timing classes of the library (index = KT_* value) and the kernels they stand for
+KT_NAMES = ("k_cg_spmv", "k_cg_update", "k_cg_rho+k_cg_pupd", "k_ic0_sweep", "k_update_line")
+SMS, FP64_FMA_PER_CLK_SM = 152, 2
+
+
+def fp64_peak_tflops(sm_mhz):
+    """FP64 peak from unit counts and clock: 152 SMs x 2 FP64 FMA per SM per clock x 2 flop
+    (GB300's nominal FP64 rate, 1.25 TFLOP/s at 2070 MHz)."""
+    return SMS * FP64_FMA_PER_CLK_SM * 2 * float(sm_mhz) * 1e6 / 1e12
+
+
+def roofline_of(kt, n, steps, ms_total, peak, peak_kind, sm_mhz=None):
+    """Roofline of the dominant kernel class. kt: {class: (total ms, launches)} over `steps`
+    steps of an n-row basin. Algorithmic bytes per launch per class (each array once); the FP64
+    SpMV is bound by the FP64 pipe (ncu: 83 % busy, DRAM 44 %), so when it dominates it is
+    reported as "alu" against the FP64 peak, with its HBM-equivalent rate beside it."""
+    per_launch_bytes = {
+        0: n * (15 * 8 + 8 + 8),            # SpMV: values, p (gathers cached), w
+        1: n * (4 * 8 + 2 * 8),             # IC0 path update: x, r, p, w read; x, r written
+        2: n * (3 * 8 + 8) / 2,             # (r, z) dot + p update, two launches
+        3: n * (2 * 8 * 8 + 4 * 8) / 16,    # IC0 colour phase: F (8 per row per sweep), r / y / z
+        4: n * (2 * 8 + 2 * 8 + 8 + 8 + 3 * 8 + 8 + 8 + 8),  # fused update + line solve
+    }
+    spmv_flops = 2 * 16 * n                 # 15 slot FMAs and the (p, Ap) FMA per row
+    live = {k: v for k, v in kt.items() if v[1] > 0}
+    dom = max(live, key=lambda k: live[k][0])
+    dom_ms, dom_launches = live[dom]
+    avg_s = dom_ms * 1e-3 / dom_launches
+    gbs = per_launch_bytes[dom] / avg_s / 1e9
+    out = {"kernel": KT_NAMES[dom], "traffic": dram_traffic(KT_NAMES[dom]),
+           "kernel_share_of_step": round(dom_ms / max(ms_total, 1e-9), 4)}
+    if dom == 0:
+        pk = fp64_peak_tflops(sm_mhz or 2070.0)
+        tf = spmv_flops / avg_s / 1e12
+        out.update({"bound": "alu", "achieved": round(tf, 4), "peak": round(pk, 4), "unit": "TFLOP/s",
+                    "frac": round(tf / pk, 4),
+                    "peak_source": f"derived: {SMS} SMs x {FP64_FMA_PER_CLK_SM} FP64 FMA/clk x 2 flop x "
+                                   f"{sm_mhz or 2070.0:.0f} MHz (nominal FP64 1.25 TFLOP/s)",
+                    "hbm_equivalent": {"achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                                       "frac": round(gbs / peak, 4), "peak_source": peak_kind}})
+    else:
+        out.update({"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(gbs / peak, 4), "peak_source": peak_kind})
+    out["classes_ms_per_step"] = {KT_NAMES[k]: round(v[0] / steps, 3) for k, v in kt.items()}
+    out["classes"] = {KT_NAMES[k]: {"launches_per_step": v[1] // max(steps, 1),
+                                    "us_per_launch": round(v[0] * 1e3 / v[1], 1),
+                                    "gbs": round(per_launch_bytes[k] / (v[0] * 1e-3 / v[1]) / 1e9, 1),
+                                    "frac": round(per_launch_bytes[k] / (v[0] * 1e-3 / v[1]) / 1e9 / peak, 4)}
+                      for k, v in live.items()}
+    return out
+
+
 def dram_traffic(kernel: str):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of `kernel` from the
     ncu summary in profiles/traffic.md, or None when the source file the counters were taken on
@@ -431,33 +483,8 @@ def run_ours(args):
 
     # roofline of the dominant kernel class, timed live with events on the solve stream
     n = op.n
-    per_launch_bytes = {
-        api.KT_SPMV: n * (15 * 8 + 8 + 8),            # values, p (gathers cached), w
-        api.KT_UPDATE: n * (4 * 8 + 2 * 8),           # IC0 path: x, r, p, w read; x, r written
-        api.KT_PUPDATE: n * (3 * 8 + 8) / 2,          # (r, z) dot + p update, two launches
-        api.KT_IC0: n * (2 * 8 * 8 + 4 * 8) / 16,     # F (8 per row per sweep), r/y/z, per launch
-        # fused update + line solve: x, r read+write, p, w, 3 Thomas factors, z, r again, m
-        api.KT_LINE: n * (2 * 8 + 2 * 8 + 8 + 8 + 3 * 8 + 8 + 8 + 8),
-    }
-    names = {api.KT_SPMV: "k_cg_spmv", api.KT_UPDATE: "k_cg_update", api.KT_PUPDATE: "k_cg_rho+k_cg_pupd",
-             api.KT_IC0: "k_ic0_sweep", api.KT_LINE: "k_update_line"}
-    dom = max(kt, key=lambda k: kt[k][0])
-    dom_ms, dom_launches = kt[dom]
     peak, peak_kind = measured_peaks()
-    avg_s = dom_ms * 1e-3 / max(dom_launches, 1)
-    achieved = per_launch_bytes[dom] / avg_s / 1e9
-    traffic = dram_traffic(names[dom])
-    roofline = {"bound": "hbm", "kernel": names[dom], "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                "peak_source": peak_kind,
-                "kernel_share_of_step": round(dom_ms / max(ms_total, 1e-9), 4),
-                "classes_ms_per_step": {names[k]: round(v[0] / args.steps, 3) for k, v in kt.items()},
-                "classes": {names[k]: {"launches_per_step": v[1] // max(args.steps, 1),
-                                       "us_per_launch": round(v[0] * 1e3 / max(v[1], 1), 1),
-                                       "gbs": round(per_launch_bytes[k] / (v[0] * 1e-3 / max(v[1], 1)) / 1e9, 1),
-                                       "frac": round(per_launch_bytes[k] / (v[0] * 1e-3 / max(v[1], 1)) / 1e9 / peak,
-                                                     4)}
-                            for k, v in kt.items() if v[1] > 0}}
+    roofline = roofline_of(kt, n, args.steps, ms_total, peak, peak_kind, (clk or {}).get("sm_mhz"))
 
     # end to end through the C ABI with host buffers: theta in, (u1, u2, u3, p) out each step
     e2e = None

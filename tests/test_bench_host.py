@@ -57,3 +57,27 @@ def test_traffic_lookup(tmp_path, monkeypatch):
     assert bench.dram_traffic("k_a") == 1234
     assert bench.dram_traffic("k_b") is None   # source changed since the capture
     assert bench.dram_traffic("k_c") is None   # not captured
+
+
+def test_roofline_of_dominant_class():
+    import bench
+    n = 5_389_312
+    # SpMV dominant: FP64-pipe bound, reported against the derived FP64 peak
+    kt = {0: (825.0, 4988), 1: (16.5, 316), 2: (171.0, 5304), 3: (191.7, 5056), 4: (800.0, 4672)}
+    r = bench.roofline_of(kt, n, 1, 2098.0, 6791.0, "measured", 2070.0)
+    assert r["bound"] == "alu" and r["kernel"] == "k_cg_spmv" and r["unit"] == "TFLOP/s"
+    pk = bench.fp64_peak_tflops(2070.0)
+    assert abs(pk - 152 * 2 * 2 * 2.07e9 / 1e12) < 1e-9
+    t = 825.0e-3 / 4988
+    assert abs(r["achieved"] - round(32 * n / t / 1e12, 4)) < 1e-9
+    assert abs(r["hbm_equivalent"]["achieved"] - round(136 * n / t / 1e9, 1)) < 1e-9
+    assert 0.6 < r["hbm_equivalent"]["frac"] < 0.7 and 0.75 < r["frac"] < 0.9
+    assert set(r["classes"]) == set(bench.KT_NAMES)
+    # fused line dominant: HBM
+    kt[4] = (900.0, 4672)
+    r = bench.roofline_of(kt, n, 1, 2098.0, 6791.0, "measured", None)
+    assert r["bound"] == "hbm" and r["kernel"] == "k_update_line" and r["unit"] == "GB/s"
+    assert abs(r["achieved"] - round(96 * n / (900e-3 / 4672) / 1e9, 1)) < 1e-9
+    # classes with no launches are left out
+    kt[1] = (0.0, 0)
+    assert "k_cg_update" not in bench.roofline_of(kt, n, 1, 2098.0, 6791.0, "measured")["classes"]
