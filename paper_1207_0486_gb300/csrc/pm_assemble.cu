@@ -344,6 +344,7 @@ int launch_dinv(pm_operator* op, int which, cudaStream_t s) {
 }
 
 int launch_ic0_factor(pm_operator* op, int which, double shift, int* breakdown, cudaStream_t s) {
+  if (which_valset(which) < 0 || !which_symmetric(which)) return set_error(PM_EINVAL, "IC0 of a non-symmetric operator");
   Ic0Factor& f = op->ic0[which];
   if (!f.F) {
     int st = cuda_check(cudaMalloc((void**)&f.F, (size_t)NSLOT * op->n * sizeof(double)), "cudaMalloc ic0");

@@ -1284,25 +1284,6 @@ __global__ void __launch_bounds__(TPB) k32_pupd(int64_t n, const float* __restri
   }
 }
 
-// Inner start: r32 = (float) r64, d32 = 0, grid (r, r) in FP64 -> inner tolerance.
-__global__ void __launch_bounds__(TPB) k32_start(int64_t n, const double* __restrict__ r64, float* __restrict__ r32,
-                                                 float* __restrict__ d32, double inner_rtol, double* partials,
-                                                 PcgScalars* sc) {
-  double v[1] = {0.0};
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const float ri = (float)r64[i];
-    r32[i] = ri;
-    d32[i] = 0.f;
-    v[0] = fma((double)ri, (double)ri, v[0]);
-  }
-  if (grid_sum<1>(v, partials, &sc->count[1]) && threadIdx.x == 0) {
-    sc->bb = v[0];
-    sc->rr = v[0];
-    sc->tol2 = inner_rtol * inner_rtol * v[0];
-    sc->done = v[0] == 0.0 ? 1 : 0;
-  }
-}
-
 __global__ void k32_from64(int64_t n, const double* __restrict__ r64, float* __restrict__ r32) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     r32[i] = (float)r64[i];
@@ -1310,11 +1291,6 @@ __global__ void k32_from64(int64_t n, const double* __restrict__ r64, float* __r
 
 __global__ void k_fill32(float* x, int64_t n, float v) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) x[i] = v;
-}
-
-__global__ void k_add_f32(int64_t n, double* __restrict__ x, const float* __restrict__ d) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    x[i] += (double)d[i];
 }
 
 template <typename T>
