@@ -278,7 +278,9 @@ enum { PM_STEP_LUMPED = 0, PM_STEP_CONSISTENT = 1 };
  *   b_c = velocity right-hand side (history, advection, Coriolis, G_c^T p^k, wind tension)
  *   (alpha M + K_nu) u~_c = b_c, c = 1..3               (velocity PCG, x0 = u^k_c)
  *   K_I q = -alpha sum_c G_c u~_c, zero mean            (pressure PCG, x0 = previous q)
- *   p^{k+1} = p^k + q;  u_c = u~_c + M^{-1} G_c q / alpha, then the Dirichlet sets
+ *   p^{k+1} = p^k + q;  u_c = u~_c - M^{-1} G_c q / alpha, then the Dirichlet sets
+ *   (the correction takes the sign of Eq. correc_velo_u, from which Eq. press_cor follows;
+ *   Eq. fofa_velo_cor_h prints "+", which would add the gradient instead of removing it)
  * theta1, theta2: device arrays [ncols], kinematic wind tension at the surface node of each
  * column (NULL = 0). correction: PM_STEP_LUMPED (diag(M 1)) or PM_STEP_CONSISTENT (PCG on M
  * with vel's options). stats: NULL or 7 entries (u1, u2, u3, q, mass1, mass2, mass3).

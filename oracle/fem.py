@@ -3,7 +3,8 @@
 Discrete problems (Section 5, Eqs. fofa_velo_pred_h to fofa_velo_cor_h) on P1 tetrahedra:
   velocity prediction  (alpha M + K_nu) u~_c = b_c        (Eq. fofa_velo_pred_h)
   pressure increment   K_I q = -alpha sum_c G_c u~_c       (Eq. fofa_q_cor_h)
-  velocity correction  M u_c = M u~_c + (1/alpha) G_c q    (Eq. fofa_velo_cor_h)
+  velocity correction  M u_c = M u~_c - (1/alpha) G_c q    (Eq. fofa_velo_cor_h, with the sign of
+                                                            Eq. correc_velo_u)
 with alpha = 3/(2 dt) for BDF2 (Eq. pred_velo) and alpha = 1/dt for the BDF1 start step.
 Element integrals (exact for P1 on a tetrahedron K with barycentric gradients grad phi_i):
   mass       M^K_ij   = |K| (1 + delta_ij) / 20

@@ -8,11 +8,22 @@ One step k -> k+1 (Eqs. fofa_velo_pred_h, fofa_q_cor_h, fofa_pres_cor_h, fofa_ve
   4. solve K_I q = b_p for mean-zero q (Lagrange-multiplier reading; PCG, Jacobi = DIAG)
   5. p^{k+1} = p^k + q   (Eq. fofa_pres_cor_h: q and p^k lie in P_h, so the L2 projection is
      the identity)
-  6. u_c = u~_c + (1/alpha) M^{-1} G_c q, then u_c = 0 on component c's Dirichlet set
+  6. u_c = u~_c - (1/alpha) M^{-1} G_c q, then u_c = 0 on component c's Dirichlet set
      (lumped M_L = diag(M 1) by default; the consistent M solved by PCG on request)
 alpha = 1/dt on the first step (BDF1 start, the paper leaves u^1 unspecified) and 3/(2 dt)
-after. Parity of the step as a whole is pinned through its parts (operators, solves) and the
-invariant that a basin at rest with no forcing stays at rest.
+after.
+
+Sign of the correction. Eq. correc_velo_u, (3/(2 dt)) (u^{k+1} - u~^{k+1}) + grad q = 0, gives
+u^{k+1} = u~^{k+1} - (2 dt / 3) grad q, and Eq. press_cor (-Lap q = -(3/(2 dt)) div u~) follows
+from it and div u^{k+1} = 0 only with that minus sign. The closing formula of Section 3 and
+Eq. fofa_velo_cor_h print "+ dt (2/3) grad q"; read literally, the correction would add the
+gradient instead of removing it and double the divergence it is meant to cancel. The oracle
+takes the minus sign that Eqs. correc_velo_u and press_cor fix.
+
+Pins (tests/test_oracle_step.py): one projection of a pure gradient field grad(phi) with
+d phi / dn = 0 on a cube removes it up to the discretisation error (the plus sign would double
+it), the corrected velocity of a wind-driven step has a smaller discrete divergence
+sum_c G_c u_c than the prediction, and a basin at rest with no forcing stays at rest.
 """
 from __future__ import annotations
 
@@ -72,6 +83,45 @@ def _precond(A, kind: str, mesh: Mesh):
     raise ValueError(kind)
 
 
+def pressure_increment(ops: fem.Operators, ut: np.ndarray, bdf1: bool, x0: Optional[np.ndarray],
+                       opts: StepOptions) -> "tuple[np.ndarray, pcgm.SolveResult]":
+    """Steps 3-4: b_p = -alpha sum_c G_c u~_c (Eq. fofa_q_cor_h) and the mean-zero solve of
+    K_I q = b_p (Lagrange-multiplier reading). Returns (b_p, result)."""
+    bp = fem.divergence_rhs(ops, ut, bdf1)
+    K = ops.A_p()
+    res = pcgm.pressure_solve(K, ops.m, bp, x0=x0, rtol=opts.pres_rtol, max_iter=opts.max_iter,
+                              precond=_precond(K, opts.pres_prec, ops.mesh))
+    return bp, res
+
+
+def correct_velocity(ops: fem.Operators, ut: np.ndarray, q: np.ndarray, a: float,
+                     opts: StepOptions) -> "tuple[np.ndarray, list]":
+    """Step 6 before the Dirichlet sets: the L2 projection of u~_c - (1/alpha) grad q onto the
+    velocity space (Eq. fofa_velo_cor_h with the sign of Eq. correc_velo_u),
+        M u_c = M u~_c - (1/alpha) G_c q,
+    with the lumped mass M_L = diag(M 1) (opts.lumped_correction) or the consistent M by PCG.
+    Returns (u, mass-solve results)."""
+    u_new = np.zeros_like(ut)
+    mass = []
+    if opts.lumped_correction:
+        ml = ops.m
+        for c in range(3):
+            u_new[c] = ut[c] - (ops.G[c] @ q) / (a * ml)
+    else:
+        for c in range(3):
+            rhs = ops.M @ ut[c] - (ops.G[c] @ q) / a
+            res = pcgm.pcg(ops.M, rhs, x0=ut[c], rtol=opts.vel_rtol, max_iter=opts.max_iter,
+                           precond=_precond(ops.M, opts.mass_prec, ops.mesh))
+            u_new[c] = res.x
+            mass.append(res)
+    return u_new, mass
+
+
+def discrete_divergence(ops: fem.Operators, u: np.ndarray) -> np.ndarray:
+    """sum_c G_c u_c: the integral of div(u) against each basis function."""
+    return sum(ops.G[c] @ u[c] for c in range(3))
+
+
 def project_step(ops: fem.Operators, st: State, opts: StepOptions = StepOptions()) -> StepReport:
     mesh = ops.mesh
     bdf1 = st.step == 0
@@ -87,26 +137,12 @@ def project_step(ops: fem.Operators, st: State, opts: StepOptions = StepOptions(
         ut[c] = res.x
         rep.vel.append(res)
     rep.u_tilde = ut
-    bp = fem.divergence_rhs(ops, ut, bdf1)
+    bp, pres = pressure_increment(ops, ut, bdf1, st.q, opts)
     rep.b_p = bp
-    K = ops.A_p()
-    pres = pcgm.pressure_solve(K, ops.m, bp, x0=st.q, rtol=opts.pres_rtol, max_iter=opts.max_iter,
-                               precond=_precond(K, opts.pres_prec, mesh))
     rep.pres = pres
     q = pres.x
     p_new = st.p + q
-    u_new = np.zeros_like(ut)
-    if opts.lumped_correction:
-        ml = ops.m
-        for c in range(3):
-            u_new[c] = ut[c] + (ops.G[c] @ q) / (a * ml)
-    else:
-        for c in range(3):
-            rhs = ops.M @ ut[c] + (ops.G[c] @ q) / a
-            res = pcgm.pcg(ops.M, rhs, x0=ut[c], rtol=opts.vel_rtol, max_iter=opts.max_iter,
-                           precond=_precond(ops.M, opts.mass_prec, mesh))
-            u_new[c] = res.x
-            rep.mass.append(res)
+    u_new, rep.mass = correct_velocity(ops, ut, q, a, opts)
     for c in range(3):
         u_new[c][mesh.dirichlet[c]] = 0.0
     st.u_prev = st.u

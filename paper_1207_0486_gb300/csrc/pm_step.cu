@@ -5,8 +5,11 @@
 //                 pressure (G_c^T p^k)_i = sum_K |K|/4 d_c phi_i sum_{j in K} p_j, and the wind
 //                 tension on Gamma_s with the surface P1 mass |F| (1 + d_ij)/12; Dirichlet rows 0
 //   k_div_rhs     b_p = -alpha sum_c G_c u~_c (Eq. fofa_q_cor_h), the three G_c on one stencil
-//   k_correct     u_c = u~_c + (G_c q)_i / (alpha m_i), lumped mass m = M 1
-//                 (Eq. fofa_velo_cor_h), then the Dirichlet sets
+//   k_correct     u_c = u~_c - (G_c q)_i / (alpha m_i), lumped mass m = M 1
+//                 (Eq. fofa_velo_cor_h), then the Dirichlet sets. The minus sign is the one
+//                 Eq. correc_velo_u fixes, (3/(2 dt)) (u - u~) + grad q = 0, and the one from
+//                 which Eq. press_cor follows; the "+" printed in Eq. fofa_velo_cor_h and at the
+//                 end of Section 3 would add the gradient the correction exists to remove.
 //   k_axpy        p^{k+1} = p^k + q (Eq. fofa_pres_cor_h: the L2 projection onto P_h is the
 //                 identity for q, p^k in P_h)
 #include <chrono>
@@ -221,7 +224,7 @@ __global__ void __launch_bounds__(TPB) k_div_rhs(Geom g, GradIn in, double alpha
   }
 }
 
-// u_c = u~_c + (G_c q)_i / (alpha m_i) on non-Dirichlet rows, 0 on Dirichlet rows.
+// u_c = u~_c - (G_c q)_i / (alpha m_i) on non-Dirichlet rows, 0 on Dirichlet rows.
 __global__ void __launch_bounds__(TPB) k_correct(Geom g, GradIn in, const double* __restrict__ q,
                                                  const double* __restrict__ m, double inv_alpha) {
   const int nz = g.nz;
@@ -246,11 +249,11 @@ __global__ void __launch_bounds__(TPB) k_correct(Geom g, GradIn in, const double
     const double sc = inv_alpha / m[row];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
-      in.out[c][row] = is_dirichlet(fl, k, nz, c) ? 0.0 : in.u[c][row] + s[c] * sc;
+      in.out[c][row] = is_dirichlet(fl, k, nz, c) ? 0.0 : fma(-s[c], sc, in.u[c][row]);
   }
 }
 
-// Right-hand side of the consistent-mass correction: M u~_c + (G_c q) / alpha.
+// Right-hand side of the consistent-mass correction: M u~_c - (G_c q) / alpha.
 __global__ void __launch_bounds__(TPB) k_correct_rhs(Geom g, GradIn in, const double* __restrict__ mval,
                                                      const double* __restrict__ q, double inv_alpha) {
   const int nz = g.nz;
@@ -277,7 +280,7 @@ __global__ void __launch_bounds__(TPB) k_correct_rhs(Geom g, GradIn in, const do
       }
     }
 #pragma unroll
-    for (int c = 0; c < 3; ++c) in.out[c][row] = mu[c] + s[c] * inv_alpha;
+    for (int c = 0; c < 3; ++c) in.out[c][row] = fma(-s[c], inv_alpha, mu[c]);
   }
 }
 
@@ -355,7 +358,7 @@ int project_step(pm_operator* op, pm_state* st, const double* th1, const double*
   k_axpy<<<G, TPB, 0, s>>>(op->n, 1.0, st->q, st->p);
   count_launch();
   if (correction == PM_STEP_CONSISTENT) {
-    // b[c] <- M u~_c + G_c q / alpha, then M u_c = b[c] by PCG with x0 = u~_c
+    // b[c] <- M u~_c - G_c q / alpha, then M u_c = b[c] by PCG with x0 = u~_c
     GradIn gr = gi;
     for (int c = 0; c < 3; ++c) gr.out[c] = st->b[c];
     k_correct_rhs<<<G, TPB, 0, s>>>(g, gr, op->d_val[VS_M], st->q, 1.0 / alpha);
