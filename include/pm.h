@@ -156,8 +156,8 @@ int pm_operator_info_get(const pm_operator* op, pm_operator_info* info);
 /* Grid indices of each ocean column (host arrays of length ncols). */
 int pm_operator_columns(const pm_operator* op, int32_t* col_i, int32_t* col_j);
 
-/* Copy one operator to host for inspection: values[s * n + row] (15 slots, see DESIGN for the
- * slot offsets), nbr[col * 7 + q] neighbour columns (-1 = none), structural slot bits per row
+/* Copy one operator to host for inspection: values[s * n + row] (15 slots at the offsets listed
+ * in api.SLOT_OFFSETS and csrc/pm_internal.cuh), nbr[col * 7 + q] neighbour columns (-1 = none), structural slot bits per row
  * (bit s set when row and slot neighbour share a tetrahedron). Any output may be NULL.
  * Dirichlet elimination is applied to the VEL values as the solver sees them. Synchronous. */
 int pm_operator_export(const pm_operator* op, pm_which which, double* values, int32_t* nbr,
@@ -175,17 +175,21 @@ int pm_pcg_solve(pm_operator* op, pm_which which, const double* b, double* x,
 
 /* Same solve as pm_pcg_solve, restricted to PM_PREC_JACOBI / PM_PREC_NONE in FP64, that
  * allocates nothing. (The paper has no counterpart: this is a deployment aid.) It is meant for
- * callers that cannot allocate device memory at solve time: code inside a CUDA stream capture
- * that must not gain allocation nodes, processes whose device memory is owned by a framework
- * allocator or a fixed pool, and embedded users that must not grow the footprint after start-up.
+ * callers that cannot allocate device memory at solve time: processes whose device memory is
+ * owned by a framework allocator or a fixed pool (an allocation behind the pool's back escapes its
+ * accounting, or fails against its reservation), and embedded users that must not grow the device
+ * footprint after start-up.
  * All scratch (Krylov vectors, Jacobi diagonal, reduction partials, device scalars) lives in one
  * static device array of PM_NOALLOC_MAX_ROWS rows (about 21 MB), held by every GPU that loads the
  * library until the process exits; no cudaMalloc, cudaFree or other allocating routine is called.
- * Systems with more than PM_NOALLOC_MAX_ROWS rows are rejected with PM_EINVAL. The first call on a
- * device looks up the array's address (cudaGetSymbolAddress) with that device current: make it
- * before any stream capture. Every call shares the one array and re-initialises what must start
- * at zero; calls that overlap on the GPU (other streams or threads) race. The operator itself
- * must already be assembled. Synchronises the stream. */
+ * Errors: PM_EINVAL for systems with more than PM_NOALLOC_MAX_ROWS rows, another preconditioner
+ * or precision, an operator that lives on a device other than the current one, or a stream that
+ * is being captured (the call reads scalars back and synchronises the stream every few
+ * iterations). The first call on a device looks up the array's address (cudaGetSymbolAddress)
+ * with that device current. Every call shares the one array and re-initialises what must start
+ * at zero; calls that overlap on the GPU (other streams or threads) race. max_iter = 0 runs no
+ * iteration (PM_NOT_CONVERGED unless x already meets rtol). The operator itself must already be
+ * assembled. Synchronises the stream. */
 #define PM_NOALLOC_MAX_ROWS 524288
 int pm_pcg_solve_noalloc(pm_operator* op, pm_which which, const double* b, double* x,
                          const pm_solve_opts* opts, pm_solve_stats* stats, pm_stream stream);

@@ -1,23 +1,27 @@
 // pm_pcg_solve_noalloc: the Jacobi / plain PCG solve with every scratch buffer taken from one
 // file-scope device array instead of allocated memory.
 //
-// Some callers cannot allocate device memory: code running under a CUDA stream capture that
-// must not add allocation nodes, hosts whose memory is owned by a custom pool or a framework
-// allocator, and embedded callers that must not grow the device footprint after start-up.
-// This entry point serves them. It calls no cudaMalloc, cudaFree, cudaMallocHost or any other
-// allocating routine (torch's included): the Krylov vectors r, p, w, the projected right-hand
-// side, the Jacobi inverse diagonal, the reduction partials and the device scalars all live in
-// g_pm_noalloc_scratch below, which every GPU that loads the library holds until the process
-// exits (about 21 MB). Host-side scalars are read into stack memory.
+// Some callers cannot allocate device memory while they solve: hosts whose device memory is
+// owned by a custom pool or a framework allocator (a cudaMalloc behind its back would escape its
+// accounting or fail against its reservation), and embedded callers that must not grow the
+// device footprint after start-up. This entry point serves them. It calls no cudaMalloc,
+// cudaFree, cudaMallocHost or any other allocating routine (torch's included): the Krylov
+// vectors r, p, w, the projected right-hand side, the Jacobi inverse diagonal, the reduction
+// partials and the device scalars all live in g_pm_noalloc_scratch below, which every GPU that
+// loads the library holds until the process exits (about 21 MB). Host-side scalars are read into
+// stack memory.
 //
 // Limits and sharing rules:
 //   - n (rows) <= PM_NOALLOC_MAX_ROWS; larger systems are rejected with PM_EINVAL.
 //   - Jacobi or no preconditioner, FP64 (the IC0 and line factors would need storage).
+//   - The operator's device must be the current device (PM_EINVAL otherwise).
+//   - The call reads convergence scalars back to the host and synchronises the stream every few
+//     iterations, so it is rejected with PM_EINVAL when the stream is being captured.
 //   - All calls on a device share the one array, which keeps the last call's contents; every
 //     call re-initialises what must start at zero (reduction tickets, scalars). Calls that
 //     overlap on the GPU (different streams, or different host threads) race on the array.
 //   - The first call on a device (with that device current) looks the array's device address up
-//     with cudaGetSymbolAddress; make that first call before any stream capture begins.
+//     with cudaGetSymbolAddress.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -196,6 +200,10 @@ __global__ void k_residual(Geom g, const double* __restrict__ val, const double*
       sc->iter = 0;
       sc->status = PM_OK;
       sc->done = (v[0] == 0.0 || v[1] <= sc->tol2) ? 1 : 0;
+      if (!sc->done && sc->max_iter == 0) {  // no iteration allowed: report the initial residual
+        sc->status = PM_NOT_CONVERGED;
+        sc->done = 1;
+      }
     } else {
       sc->aux[0] = v[1];
       sc->aux[1] = v[2];
@@ -459,6 +467,18 @@ extern "C" int pm_pcg_solve_noalloc(pm_operator* op, pm_which which, const doubl
   if (op->n > na::MAXR)
     return set_error(PM_EINVAL, "pm_pcg_solve_noalloc: the system has " + std::to_string(op->n) +
                                     " rows, more than PM_NOALLOC_MAX_ROWS = " + std::to_string(na::MAXR));
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  int st = cuda_check(cudaStreamIsCapturing(s, &cap), "cudaStreamIsCapturing");
+  if (st) return st;
+  if (cap != cudaStreamCaptureStatusNone)
+    return set_error(PM_EINVAL, "pm_pcg_solve_noalloc synchronises its stream; it cannot be called on a stream "
+                                "that is being captured");
+  int dev = -1;
+  if ((st = cuda_check(cudaGetDevice(&dev), "cudaGetDevice"))) return st;
+  if (dev != op->device)
+    return set_error(PM_EINVAL, "pm_pcg_solve_noalloc: the operator lives on device " + std::to_string(op->device) +
+                                    ", the current device is " + std::to_string(dev));
   double* base = na::scratch_for_current_device();
   if (!base) return PM_ECUDA;
   na::View v;
@@ -469,7 +489,6 @@ extern "C" int pm_pcg_solve_noalloc(pm_operator* op, pm_which which, const doubl
   v.dinv = base + na::OFF_DINV;
   v.part = base + na::OFF_PART;
   v.sc = reinterpret_cast<PcgScalars*>(base + na::OFF_SC);
-  cudaStream_t s = (cudaStream_t)stream;
   switch (which_mask((int)which)) {
     case 0: return na::run<0>(op, (int)which, b, x, opts, stats, s, v);
     case 1: return na::run<1>(op, (int)which, b, x, opts, stats, s, v);

@@ -292,6 +292,10 @@ __global__ void __launch_bounds__(TPB) k_cg_residual(Geom g, const double* __res
       sc->iter = 0;
       sc->status = PM_OK;
       sc->done = (v[0] == 0.0 || v[1] <= sc->tol2) ? 1 : 0;
+      if (!sc->done && sc->max_iter == 0) {  // no iteration allowed: report the initial residual
+        sc->status = PM_NOT_CONVERGED;
+        sc->done = 1;
+      }
     } else {
       sc->aux[0] = v[1];
       sc->aux[1] = v[2];
@@ -1710,6 +1714,10 @@ int mixed_run(pm_operator* op, int which, const double* b, double* x, const pm_s
   if (c->sc_host->zero_rhs) {
     k_fill<<<G, TPB, 0, s>>>(x, op->n, 0.0);
     count_launch();
+  } else if (c->sc_host->done) {
+    // x0 already meets rtol (PM_OK), or max_iter = 0 (PM_NOT_CONVERGED): no inner solve runs
+    status = c->sc_host->status;
+    rel_true = std::sqrt(c->sc_host->rr / bb);
   } else {
     // One CG process with reliable updates: x in FP64; r, p, w, z in FP32; dots, alpha and beta
     // in FP64. The FP32 recursive residual is replaced by the FP64 true residual b - A x each
