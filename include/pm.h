@@ -166,6 +166,18 @@ int pm_operator_export(const pm_operator* op, pm_which which, double* values, in
 /* y = A x for one operator (VEL_* with its Dirichlet elimination), device vectors. Async. */
 int pm_spmv(pm_operator* op, pm_which which, const double* x, double* y, pm_stream stream);
 
+/* r = b - A x for one operator (VEL_* with its Dirichlet elimination), every row formed in
+ * compensated arithmetic: the Dot2 scheme of Ogita, Rump and Oishi ("Accurate sum and dot
+ * product", SIAM J. Sci. Comput. 26, 2005) splits each product a_ij x_j exactly into p + e with
+ * one FMA, sums the p by TwoSum and carries both rounding errors, so r is as accurate as if formed
+ * in twice the working precision and rounded once. This is how the solvers measure the true
+ * residual. b, x, r: device vectors of length n (r must not alias x). norms: NULL (the call is
+ * asynchronous) or a host array of 3 that receives ||r||^2, || |A||x| + |b| ||^2 (the square of
+ * the FP64 floor's numerator) and ||b||^2; the call then synchronises the stream. The paper
+ * states no stopping rule; this measures the one the solvers use (Section 5 remark). */
+int pm_residual(pm_operator* op, pm_which which, const double* b, const double* x, double* r,
+                double* norms, pm_stream stream);
+
 /* Solve A x = b by PCG (Section 5 remark). For PM_OP_PRESSURE the zero-mean Lagrange multiplier
  * reading applies: b is replaced by b - (1'b / 1'm) m (m = M 1), the iterate is kept on
  * m'x = 0, and the returned x has m'x = 0. b and x are device vectors of length n; b is not
@@ -275,6 +287,16 @@ int pm_state_get(const pm_state* st, double* u1, double* u2, double* u3, double*
 int pm_state_set(pm_state* st, const double* u1, const double* u2, const double* u3,
                  const double* p, int32_t step_index, pm_stream stream);
 int32_t pm_state_step_index(const pm_state* st);
+
+/* One field of the state, copied to a caller device vector of length n. Async. Besides u^k,
+ * u^{k-1} and p^k, the last step's intermediate fields stay available until the next step: the
+ * prediction u~ (Eq. fofa_velo_pred_h), the pressure increment q and its right-hand side
+ * b_p = -alpha sum_c G_c u~_c (Eq. fofa_q_cor_h). Before the first step they are 0. */
+enum { PM_FIELD_U1 = 0, PM_FIELD_U2 = 1, PM_FIELD_U3 = 2,
+       PM_FIELD_U1_PREV = 3, PM_FIELD_U2_PREV = 4, PM_FIELD_U3_PREV = 5,
+       PM_FIELD_P = 6, PM_FIELD_Q = 7, PM_FIELD_UT1 = 8, PM_FIELD_UT2 = 9, PM_FIELD_UT3 = 10,
+       PM_FIELD_BP = 11 };
+int pm_state_field(const pm_state* st, int32_t field, double* dst, pm_stream stream);
 
 enum { PM_STEP_LUMPED = 0, PM_STEP_CONSISTENT = 1 };
 

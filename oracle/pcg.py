@@ -11,10 +11,19 @@ the textbook order of Saad's preconditioned CG:
         p_{j+1} = z_{j+1} + beta_j p_j
 At exit the true residual ||b - A x|| / ||b|| is computed; if it exceeds rtol the iteration
 restarts from the true residual (at most max_restarts times). b = 0 returns x = 0.
-The paper states no stopping rule. Besides rtol, a solve is accepted when its true residual is
-already below the floor that rounding x to FP64 alone causes, u || |A||x| + |b| ||_2 / ||b||_2
-with u = 2^-53 (backward error at the unit roundoff: no restart can go lower). On the thin ocean
-basins' pressure system this floor is near 1e-7, above a 1e-8 target.
+Every true residual r = b - A x (start, restarts, exit) is computed with the compensated dot
+product Dot2 of Ogita, Rump and Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput. 26,
+2005): each product a_ij x_j is split exactly into p + e (TwoProduct, with Veltkamp-Dekker
+splitting), the p are summed by TwoSum and every rounding error is carried, so r is as accurate
+as if b - A x were formed in twice the working precision and then rounded. The plain FP64
+residual of a nearly converged x is itself wrong by up to u || |A||x| ||, which on the thin
+basins' pressure system is of the order of the target.
+The paper states no stopping rule. Besides rtol, a solve is accepted when its (exact) true
+residual is below the floor that rounding x to FP64 alone can cause,
+u || |A||x| + |b| ||_2 / ||b||_2 with u = 2^-53 (backward error at the unit roundoff), and
+restarts no longer lower it: a restart that does not halve the true residual, or the last
+restart allowed. On the thin ocean basins' pressure system this floor is near 1e-7, above a
+1e-8 target.
 
 Preconditioners:
   Jacobi ("DIAG" of the Section 5 remark, and the labelled fallback): P = diag(A).
@@ -28,7 +37,10 @@ Pressure (Section 5 remark, zero-mean Lagrange multiplier): the augmented system
 
 Pins (tests/test_oracle_pcg.py): dense Cholesky and dense augmented solves on small meshes,
 the IC0 defining property (L L^T)_ij = A_ij on the pattern, iteration counts equal to scipy's
-cg with the same preconditioner, A-conjugacy of the search directions.
+cg with the same preconditioner, A-conjugacy of the search directions. tests/test_oracle_exact.py:
+TwoSum and TwoProduct are error-free and the compensated residual equals b - A x computed in
+exact rational arithmetic (to one rounding), where the plain FP64 residual is wrong; the floor
+bounds the exact residual of the correctly rounded solution of small systems.
 """
 from __future__ import annotations
 
@@ -39,6 +51,60 @@ import numpy as np
 import scipy.sparse as sp
 
 from . import native
+
+
+# ---- compensated residual (Ogita, Rump & Oishi 2005: TwoSum, TwoProduct, Dot2) ------------------
+
+_SPLITTER = 134217729.0   # 2^27 + 1: Veltkamp's constant for 53-bit significands
+
+
+def two_sum(a, b):
+    """s = fl(a + b) and the exact error e, a + b = s + e (Knuth's TwoSum, no branch)."""
+    s = a + b
+    bv = s - a
+    return s, (a - (s - bv)) + (b - bv)
+
+
+def split(a):
+    """a = hi + lo exactly, hi and lo with at most 26 significant bits (Veltkamp)."""
+    c = _SPLITTER * a
+    hi = c - (c - a)
+    return hi, a - hi
+
+
+def two_product(a, b):
+    """p = fl(a b) and the exact error e, a b = p + e (Dekker's TwoProduct on split halves)."""
+    p = a * b
+    ah, al = split(a)
+    bh, bl = split(b)
+    return p, al * bl - (((p - ah * bh) - al * bh) - ah * bl)
+
+
+def residual_dot2(A: sp.csr_matrix, x: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """r = b - A x with Dot2 per row: the sum b_i - sum_j a_ij x_j is formed from the exact
+    products (TwoProduct) by TwoSum, and the errors of both are accumulated and added at the
+    end. Vectorised over rows, the terms of a row taken in stored (column) order."""
+    A = A.tocsr()
+    n = A.shape[0]
+    cnt = np.diff(A.indptr)
+    rows = np.repeat(np.arange(n), cnt)
+    pos = np.arange(len(A.indices)) - A.indptr[rows]
+    s = np.array(b, dtype=np.float64, copy=True)
+    c = np.zeros(n)
+    for k in range(int(cnt.max()) if n else 0):
+        sel = pos == k
+        r_k = rows[sel]
+        p, e = two_product(A.data[sel], x[A.indices[sel]])
+        t, q = two_sum(s[r_k], -p)
+        s[r_k] = t
+        c[r_k] += q - e
+    return s + c
+
+
+def residual_floor(A: sp.spmatrix, x: np.ndarray, b: np.ndarray) -> float:
+    """u || |A||x| + |b| ||_2 / ||b||_2 with u = 2^-53: the relative residual that rounding x (and
+    b) to FP64 alone can cause, row by row u (|A||x| + |b|)_i."""
+    return 2.0 ** -53 * float(np.linalg.norm(abs(A) @ np.abs(x) + np.abs(b))) / float(np.linalg.norm(b))
 
 
 @dataclass
@@ -186,8 +252,9 @@ def pcg(A, b: np.ndarray, x0: Optional[np.ndarray] = None, rtol: float = 1e-8, m
     restarts = 0
     first_pass = None
     hist, alphas, betas = [], [], []
+    prev_true = None
     while True:
-        r = b - A @ x
+        r = residual_dot2(A, x, b)
         rnorm = float(np.sqrt(r @ r))
         converged = rnorm <= tol
         if not converged:
@@ -217,12 +284,15 @@ def pcg(A, b: np.ndarray, x0: Optional[np.ndarray] = None, rtol: float = 1e-8, m
                 p = z + beta * p
         if first_pass is None:
             first_pass = iters
-        true_res = float(np.linalg.norm(b - A @ x)) / bnorm
-        floor = 2.0 ** -53 * float(np.linalg.norm(abs(A) @ np.abs(x) + np.abs(b))) / bnorm
-        ok = true_res <= max(rtol, floor)
-        if ok or restarts >= max_restarts or iters >= max_iter:
+        true_res = float(np.linalg.norm(residual_dot2(A, x, b))) / bnorm
+        floor = residual_floor(A, x, b)
+        stalled = prev_true is not None and true_res > 0.5 * prev_true
+        last = restarts >= max_restarts or iters >= max_iter
+        ok = true_res <= rtol or (true_res <= floor and (stalled or last))
+        if ok or last:
             return SolveResult(x, iters, restarts, true_res, rnorm / bnorm, ok,
                                hist, alphas, betas, first_pass, floor)
+        prev_true = true_res
         restarts += 1
 
 

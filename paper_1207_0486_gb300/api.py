@@ -24,6 +24,8 @@ OP_VEL1_U1, OP_VEL1_U2, OP_VEL1_U3, OP_GRAD_X, OP_GRAD_Y, OP_GRAD_Z = 5, 6, 7, 8
 PREC_JACOBI, PREC_IC0, PREC_NONE, PREC_LINE = 0, 1, 2, 3
 FP64, FP32_REFINE, BF16_REFINE = 0, 1, 2
 STEP_LUMPED, STEP_CONSISTENT = 0, 1
+(FIELD_U1, FIELD_U2, FIELD_U3, FIELD_U1_PREV, FIELD_U2_PREV, FIELD_U3_PREV, FIELD_P, FIELD_Q,
+ FIELD_UT1, FIELD_UT2, FIELD_UT3, FIELD_BP) = range(12)
 
 # Slot offsets (di, dj, dk) of the 15-slot layout, in slot order (documented in pm.h's layout).
 SLOT_OFFSETS = [(0, 0, -1), (0, 0, 0), (0, 0, 1), (1, 0, 0), (1, 0, 1), (-1, 0, -1), (-1, 0, 0),
@@ -74,12 +76,14 @@ SIGNATURES = {
     "pm_operator_columns": (_I, [_P, _P, _P]),
     "pm_operator_export": (_I, [_P, _I, _P, _P, _P]),
     "pm_spmv": (_I, [_P, _I, _P, _P, _P]),
+    "pm_residual": (_I, [_P, _I, _P, _P, _P, _P, _P]),
     "pm_pcg_solve": (_I, [_P, _I, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), _P]),
     "pm_pcg_solve_noalloc": (_I, [_P, _I, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats), _P]),
     "pm_state_create": (_I, [_P, ctypes.POINTER(_P)]),
     "pm_state_get": (_I, [_P, _P, _P, _P, _P, _P]),
     "pm_state_set": (_I, [_P, _P, _P, _P, _P, ctypes.c_int32, _P]),
     "pm_state_step_index": (ctypes.c_int32, [_P]),
+    "pm_state_field": (_I, [_P, ctypes.c_int32, _P, _P]),
     "pm_project_step": (_I, [_P, _P, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveOpts),
                              ctypes.c_int32, _P, _P]),
     "pm_operator_destroy": (None, [_P]),
@@ -237,6 +241,14 @@ class Operator:
         _check(load().pm_spmv(self.handle, which, _dptr(x, self.n, "x"), _dptr(y, self.n, "y"),
                               _stream(stream)), "spmv")
 
+    def residual(self, which: int, b, x, r, stream=None, norms: bool = True):
+        """pm_residual: r = b - A x in compensated arithmetic. Returns (||r||^2, || |A||x| + |b| ||^2,
+        ||b||^2) when norms is true (synchronising), else None."""
+        nb = (ctypes.c_double * 3)() if norms else None
+        _check(load().pm_residual(self.handle, which, _dptr(b, self.n, "b"), _dptr(x, self.n, "x"),
+                                  _dptr(r, self.n, "r"), nb, _stream(stream)), "residual")
+        return (nb[0], nb[1], nb[2]) if norms else None
+
     def solve(self, which: int, b, x, opts: Options = Options(), stream=None, allow_not_converged=False):
         st = SolveStats()
         o = opts.c()
@@ -313,6 +325,13 @@ class State:
         n = self.op.n
         out = [torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(4)]
         _check(load().pm_state_get(self.handle, *[_dptr(t) for t in out], _stream(stream)), "state_get")
+        return out
+
+    def field(self, which: int, out=None, stream=None):
+        """pm_state_field: one state field (FIELD_*) as a CUDA float64 tensor."""
+        torch = _torch()
+        out = torch.empty(self.op.n, dtype=torch.float64, device="cuda") if out is None else out
+        _check(load().pm_state_field(self.handle, which, _dptr(out, self.op.n, "out"), _stream(stream)), "state_field")
         return out
 
     def set(self, u1=None, u2=None, u3=None, p=None, step_index=0, stream=None):

@@ -282,6 +282,12 @@ int pm_spmv(pm_operator* op, pm_which which, const double* x, double* y, pm_stre
   return spmv(op, (int)which, x, y, (cudaStream_t)stream);
 }
 
+int pm_residual(pm_operator* op, pm_which which, const double* b, const double* x, double* r, double* norms,
+                pm_stream stream) {
+  if (!op || !b || !x || !r) return set_error(PM_EINVAL, "null argument");
+  return residual(op, (int)which, b, x, r, norms, (cudaStream_t)stream);
+}
+
 int pm_pcg_solve(pm_operator* op, pm_which which, const double* b, double* x,
                  const pm_solve_opts* opts, pm_solve_stats* stats, pm_stream stream) {
   if (!op || !b || !x || !opts) return set_error(PM_EINVAL, "null argument");
@@ -321,6 +327,22 @@ int pm_state_get(const pm_state* st, double* u1, double* u2, double* u3, double*
       if (r) return r;
     }
   return PM_OK;
+}
+
+int pm_state_field(const pm_state* st, int32_t field, double* dst, pm_stream stream) {
+  if (!st || !dst) return set_error(PM_EINVAL, "null argument");
+  const double* src = nullptr;
+  switch (field) {
+    case PM_FIELD_U1: case PM_FIELD_U2: case PM_FIELD_U3: src = st->u[field - PM_FIELD_U1]; break;
+    case PM_FIELD_U1_PREV: case PM_FIELD_U2_PREV: case PM_FIELD_U3_PREV: src = st->u_prev[field - PM_FIELD_U1_PREV]; break;
+    case PM_FIELD_P: src = st->p; break;
+    case PM_FIELD_Q: src = st->q; break;
+    case PM_FIELD_UT1: case PM_FIELD_UT2: case PM_FIELD_UT3: src = st->ut[field - PM_FIELD_UT1]; break;
+    case PM_FIELD_BP: src = st->bp; break;
+    default: return set_error(PM_EINVAL, "unknown state field");
+  }
+  return cuda_check(cudaMemcpyAsync(dst, src, st->op->n * sizeof(double), cudaMemcpyDeviceToDevice,
+                                    (cudaStream_t)stream), "state field");
 }
 
 int pm_state_set(pm_state* st, const double* u1, const double* u2, const double* u3, const double* p,

@@ -58,6 +58,7 @@ struct Sys {
 
 struct Scal {
   double rho, alpha, beta, rr, bb, tol2, inner_tol2, proj_c, rel_true, rel_floor, rtol, inner_rtol;
+  double prev_true;  // true residual of the previous REFINE (-1: none yet)
   int32_t iter, outer, state, status, max_iter, first_pass;
 };
 
@@ -225,48 +226,8 @@ __device__ __forceinline__ double spmv_tile(const Sys& S, int row0, int rows, in
   return acc;
 }
 
-// FP64 row with |A||x| (true residual and its floor); MASKC as row_spmv.
-template <int MASKC>
-__device__ __forceinline__ double row_apply64_abs(const Geom& g, const double* __restrict__ val, const double* x,
-                                                  int row, int col, int k, double& asum) {
-  constexpr bool MASK = MASKC >= 0;
-  const int nz = g.nz, npad = (int)g.npad;
-  int nb[NNBR];
-  nb[0] = col;
-#pragma unroll
-  for (int q = 1; q < NNBR; ++q) nb[q] = __ldg(g.nbr + col * NNBR + q);
-  double a[NSLOT];
-#pragma unroll
-  for (int s = 0; s < NSLOT; ++s) a[s] = __ldg(val + s * npad + row);
-  uint8_t fl[NNBR];
-  if (MASK) {
-#pragma unroll
-    for (int q = 0; q < NNBR; ++q) fl[q] = __ldg(g.colflag + (nb[q] >= 0 ? nb[q] : col));
-  }
-  const double xi = x[row];
-  if (MASK && is_dirichlet(fl[0], k, nz, MASKC)) {
-    asum = fabs(xi);
-    return xi;
-  }
-  double sum = 0.0;
-  asum = 0.0;
-#pragma unroll
-  for (int s = 0; s < NSLOT; ++s) {
-    const int q = slot_q(s), kk = k + slot_dk(s);
-    bool ok = nb[q] >= 0;
-    if (slot_dk(s) < 0) ok = ok && kk >= 0;
-    if (slot_dk(s) > 0) ok = ok && kk < nz;
-    const bool keep = MASK ? ok && !is_dirichlet(fl[q], kk, nz, MASKC) : ok;
-    const double av = keep ? a[s] : 0.0;
-    const double xv = x[ok ? nb[q] * nz + kk : row];
-    sum = fma(av, xv, sum);
-    asum += fabs(av * xv);
-  }
-  return sum;
-}
-
-// Phase A of a REFINE system's tile: r = b' - A x in FP64, partials of (r, r) and of the floor
-// (|A||x| + |b|)^2.
+// Phase A of a REFINE system's tile: r = b' - A x in FP64, compensated (row_residual_dot2), and
+// partials of (r, r) and of the floor (|A||x| + |b|)^2.
 template <typename T, int MASKC>
 __device__ __forceinline__ void refine_tile(const Sys& S, int row0, int rows, int nz, double& rr, double& ff) {
   T* r = (T*)S.r;
@@ -274,9 +235,8 @@ __device__ __forceinline__ void refine_tile(const Sys& S, int row0, int rows, in
   for (int i = threadIdx.x; i < rows; i += blockDim.x) {
     const int row = row0 + i, col = row / nz, k = row - col * nz;
     double asum;
-    const double ax = row_apply64_abs<MASKC>(g, S.val64, S.x, row, col, k, asum);
     const double bi = S.bw[row];
-    const double ri = bi - ax;
+    const double ri = row_residual_dot2<MASKC>(g, S.val64, S.x, bi, row, col, k, asum);
     r[row] = (T)ri;
     rr = fma(ri, ri, rr);
     const double f = asum + fabs(bi);
@@ -477,6 +437,7 @@ __global__ void __launch_bounds__(256, PM_BATCH_MINB) k_batch(const Sys* __restr
         c.status = PM_OK;
         c.state = tot[0] == 0.0 ? ST_DONE : ST_PINIT;
         c.rel_true = 0.0;
+        c.prev_true = -1.0;
       }
     }
     if (!grid_barrier(ctl)) return;
@@ -546,9 +507,13 @@ __global__ void __launch_bounds__(256, PM_BATCH_MINB) k_batch(const Sys* __restr
           c.outer += 1;
           c.rel_true = sqrt(a0 / c.bb);
           c.rel_floor = ldexp(1.0, -53) * sqrt(a1 / c.bb);
-          if (c.rel_true <= fmax(c.rtol, c.rel_floor)) {
+          // done at rtol, or below the FP64 floor once a restart no longer halves the residual
+          const bool stalled = c.prev_true >= 0.0 && c.rel_true > 0.5 * c.prev_true;
+          const bool last = c.iter >= c.max_iter || c.outer > 64;
+          c.prev_true = c.rel_true;
+          if (c.rel_true <= c.rtol || (c.rel_true <= c.rel_floor && (stalled || last))) {
             c.state = S.proj ? ST_SHIFT : ST_DONE;
-          } else if (c.iter >= c.max_iter || c.outer > 64) {
+          } else if (last) {
             c.status = PM_NOT_CONVERGED;
             c.state = S.proj ? ST_SHIFT : ST_DONE;
           } else {

@@ -80,6 +80,22 @@ __host__ __device__ inline bool is_dirichlet(uint8_t flag, int k, int nz, int c)
   return k == nz - 1;
 }
 
+// ---- compensated residual (Ogita, Rump & Oishi, "Accurate sum and dot product", 2005) --------
+// Error-free transformations in FP64. The _rn intrinsics are never contracted into an FMA, which
+// would change what the transformations compute.
+__device__ __forceinline__ double two_sum(double a, double b, double& err) {
+  const double s = __dadd_rn(a, b);
+  const double bv = __dsub_rn(s, a);
+  err = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bv)), __dsub_rn(b, bv));
+  return s;
+}
+// a * b = p + err exactly (one FMA gives the rounding error of the product).
+__device__ __forceinline__ double two_product(double a, double b, double& err) {
+  const double p = __dmul_rn(a, b);
+  err = fma(a, b, -p);
+  return p;
+}
+
 // Device view of a basin's mesh.
 struct Geom {
   int32_t ncols, nz;
@@ -91,6 +107,55 @@ struct Geom {
   const uint8_t* colflag;   // [ncols] CF_*
   const double* coriolis;   // [ncols] or null
 };
+
+// r_i = b_i - (A x)_i for one row of the column-sliced operator, by Dot2 (Ogita, Rump & Oishi):
+// every product a_ij x_j is split exactly into p + e (two_product), the -p are summed into b_i by
+// two_sum, and both rounding errors are accumulated and added once at the end. The result is as
+// accurate as b_i - (A x)_i formed in twice the working precision and rounded once; the plain
+// FP64 residual of a nearly converged x is wrong by up to u (|A||x|)_i, which for the thin
+// basins' pressure operator is of the order of the residuals a solve aims for.
+// abs_sum receives (|A||x|)_i (the FP64 floor). MASKC >= 0: component MASKC's symmetric
+// Dirichlet elimination (identity row, zero column), as the solvers apply it.
+template <int MASKC>
+__device__ __forceinline__ double row_residual_dot2(const Geom& g, const double* __restrict__ val,
+                                                    const double* x, double bi, int row, int col, int k,
+                                                    double& abs_sum) {
+  const int nz = g.nz;
+  const int npad = (int)g.npad;
+  int nb[NNBR];
+  uint8_t fl[NNBR];
+  nb[0] = col;
+#pragma unroll
+  for (int q = 1; q < NNBR; ++q) nb[q] = __ldg(g.nbr + col * NNBR + q);
+  if (MASKC >= 0) {
+#pragma unroll
+    for (int q = 0; q < NNBR; ++q) fl[q] = __ldg(g.colflag + (nb[q] >= 0 ? nb[q] : col));
+    if (is_dirichlet(fl[0], k, nz, MASKC)) {
+      const double xi = x[row];
+      abs_sum = fabs(xi);
+      return __dsub_rn(bi, xi);
+    }
+  }
+  double s = bi, c = 0.0, asum = 0.0;
+#pragma unroll
+  for (int sl = 0; sl < NSLOT; ++sl) {
+    const int q = slot_q(sl);
+    const int kk = k + slot_dk(sl);
+    bool ok = nb[q] >= 0;
+    if (slot_dk(sl) < 0) ok = ok && kk >= 0;
+    if (slot_dk(sl) > 0) ok = ok && kk < nz;
+    if (MASKC >= 0) ok = ok && !is_dirichlet(fl[q], kk, nz, MASKC);
+    const double av = ok ? __ldg(val + sl * npad + row) : 0.0;
+    const double xv = x[ok ? nb[q] * nz + kk : row];
+    double pe, se;
+    const double p = two_product(av, xv, pe);
+    s = two_sum(s, -p, se);
+    c = __dadd_rn(c, __dsub_rn(se, pe));
+    asum += fabs(p);
+  }
+  abs_sum = asum;
+  return __dadd_rn(s, c);
+}
 
 // Operator value sets held per basin.
 enum ValSet { VS_AU2 = 0, VS_AU1 = 1, VS_KI = 2, VS_M = 3, VS_G0 = 4, VS_G1 = 5, VS_G2 = 6, VS_COUNT = 7 };
@@ -206,6 +271,8 @@ int launch_dinv(pm_operator* op, int which, cudaStream_t s);
 
 // pm_solve.cu
 int spmv(pm_operator* op, int which, const double* x, double* y, cudaStream_t s);
+int residual(pm_operator* op, int which, const double* b, const double* x, double* r, double* norms,
+             cudaStream_t s);
 int pcg_solve(pm_operator* op, int which, const double* b, double* x, const pm_solve_opts* o,
               pm_solve_stats* st, cudaStream_t s);
 void destroy_ctx(pm_operator* op);

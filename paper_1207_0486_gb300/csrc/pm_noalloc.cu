@@ -112,12 +112,9 @@ __device__ __forceinline__ bool done_(const PcgScalars* sc) { return *((volatile
 
 template <int MASKC>
 __device__ __forceinline__ double row_dot(const Geom& g, const double* __restrict__ val, const double* __restrict__ x,
-                                          int64_t row, int col, int k, double* abs_sum) {
+                                          int64_t row, int col, int k) {
   const int nz = g.nz;
-  if (MASKC >= 0 && is_dirichlet(g.colflag[col], k, nz, MASKC)) {
-    if (abs_sum) *abs_sum = fabs(x[row]);
-    return x[row];
-  }
+  if (MASKC >= 0 && is_dirichlet(g.colflag[col], k, nz, MASKC)) return x[row];
   int nb[NNBR];
   uint8_t fl[NNBR];
 #pragma unroll
@@ -125,19 +122,15 @@ __device__ __forceinline__ double row_dot(const Geom& g, const double* __restric
     nb[q] = q == 0 ? col : g.nbr[(int64_t)col * NNBR + q];
     if (MASKC >= 0) fl[q] = nb[q] >= 0 ? g.colflag[nb[q]] : 0;
   }
-  double sum = 0.0, asum = 0.0;
+  double sum = 0.0;
 #pragma unroll
   for (int s = 0; s < NSLOT; ++s) {
     const int q = slot_q(s);
     const int kk = k + slot_dk(s);
     if (nb[q] < 0 || kk < 0 || kk >= nz) continue;
     if (MASKC >= 0 && is_dirichlet(fl[q], kk, nz, MASKC)) continue;
-    const double a = val[(int64_t)s * g.npad + row];
-    const double xv = x[(int64_t)nb[q] * nz + kk];
-    sum = fma(a, xv, sum);
-    asum += fabs(a * xv);
+    sum = fma(val[(int64_t)s * g.npad + row], x[(int64_t)nb[q] * nz + kk], sum);
   }
-  if (abs_sum) *abs_sum = asum;
   return sum;
 }
 
@@ -181,8 +174,8 @@ __global__ void k_residual(Geom g, const double* __restrict__ val, const double*
   for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < g.n; row += (int64_t)gridDim.x * blockDim.x) {
     const int col = (int)(row / g.nz), k = (int)(row - (int64_t)col * g.nz);
     double asum = 0.0;
-    const double ax = row_dot<MASKC>(g, val, x, row, col, k, MODE == 1 ? &asum : nullptr);
-    const double bi = bw[row], ri = bi - ax;
+    const double bi = bw[row];
+    const double ri = row_residual_dot2<MASKC>(g, val, x, bi, (int)row, col, k, asum);   // compensated
     r[row] = ri;
     v[0] = fma(bi, bi, v[0]);
     v[1] = fma(ri, ri, v[1]);
@@ -253,7 +246,7 @@ __global__ void k_spmv_dot(Geom g, const double* __restrict__ val, const double*
   double v[1] = {0.0};
   for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < g.n; row += (int64_t)gridDim.x * blockDim.x) {
     const int col = (int)(row / g.nz), k = (int)(row - (int64_t)col * g.nz);
-    const double wi = row_dot<MASKC>(g, val, p, row, col, k, nullptr);
+    const double wi = row_dot<MASKC>(g, val, p, row, col, k);
     w[row] = wi;
     v[0] = fma(p[row], wi, v[0]);
   }
@@ -386,7 +379,8 @@ int run(pm_operator* op, int which, const double* b, double* x, const pm_solve_o
   count_launch(6);
   if ((st = read())) return st;
   int restarts = 0, first_pass = 0, status = PM_OK;
-  double rel_true = 0.0, rel_floor = 0.0;
+  double rel_true = 0.0, rel_floor = 0.0, prev_true = -1.0;
+  bool accepted = false;
   if (h.zero_rhs) {
     k_fill<<<G, TPB, 0, s>>>(x, n, 0.0);
     count_launch();
@@ -415,8 +409,12 @@ int run(pm_operator* op, int which, const double* b, double* x, const pm_solve_o
       if ((st = read())) return st;
       rel_true = std::sqrt(h.aux[0] / h.bb);
       rel_floor = std::ldexp(1.0, -53) * std::sqrt(h.aux[1] / h.bb);
-      if (status != PM_OK || rel_true <= std::max(o->rtol, rel_floor) || restarts >= o->max_restarts || h.iter >= o->max_iter)
-        break;
+      // as pm_pcg_solve: rtol met, or below the FP64 floor once restarts stop halving it
+      const bool stalled = prev_true >= 0.0 && rel_true > 0.5 * prev_true;
+      const bool last = restarts >= o->max_restarts || h.iter >= o->max_iter;
+      accepted = rel_true <= o->rtol || (rel_true <= rel_floor && (stalled || last));
+      if (status != PM_OK || accepted || last) break;
+      prev_true = rel_true;
       ++restarts;
       h.done = 0;
       h.rr = h.aux[0];
@@ -425,7 +423,7 @@ int run(pm_operator* op, int which, const double* b, double* x, const pm_solve_o
       count_launch(2);
       if ((st = read())) return st;
     }
-    if (status == PM_OK && rel_true > std::max(o->rtol, rel_floor)) status = PM_NOT_CONVERGED;
+    if (status == PM_OK && !accepted) status = PM_NOT_CONVERGED;
   }
   if (proj) {
     k_press_sums<<<G, TPB, 0, s>>>(n, b, x, op->d_m, 1, v.part, v.sc);

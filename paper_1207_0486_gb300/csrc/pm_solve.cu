@@ -176,9 +176,9 @@ __device__ __forceinline__ bool sc_done(const PcgScalars* sc) {
 // Branch-free: all 15 value loads are unconditional (absent slots hold 0), an absent or
 // eliminated neighbour reads x[row] and multiplies a selected 0, so every load of a row can be
 // in flight at once. 32-bit indices: the library caps n so that 15 * n_pad < 2^31.
-template <int MASKC, typename TV, typename TX, bool ABS = false>
+template <int MASKC, typename TV, typename TX>
 __device__ __forceinline__ double row_dot(const Geom& g, const TV* __restrict__ val, const TX* __restrict__ x,
-                                          int row, int col, int k, bool& is_dir, double* abs_sum = nullptr) {
+                                          int row, int col, int k, bool& is_dir) {
   const int nz = g.nz;
   const int npad = (int)g.npad;
   int nb[NNBR];
@@ -193,7 +193,7 @@ __device__ __forceinline__ double row_dot(const Geom& g, const TV* __restrict__ 
   TV a[NSLOT];
 #pragma unroll
   for (int s = 0; s < NSLOT; ++s) a[s] = __ldg(val + s * npad + row);
-  double sum = 0.0, asum = 0.0;
+  double sum = 0.0;
 #pragma unroll
   for (int s = 0; s < NSLOT; ++s) {
     const int q = slot_q(s);
@@ -205,16 +205,11 @@ __device__ __forceinline__ double row_dot(const Geom& g, const TV* __restrict__ 
     const double xv = (double)x[ok ? nb[q] * nz + kk : row];
     const double av = ok ? (double)a[s] : 0.0;
     sum = fma(av, xv, sum);
-    if (ABS) asum += fabs(av * xv);
   }
   if (MASKC >= 0) {
     is_dir = is_dirichlet(fl[0], k, nz, MASKC);
-    if (is_dir) {
-      sum = (double)x[row];
-      asum = fabs(sum);
-    }
+    if (is_dir) sum = (double)x[row];
   }
-  if (ABS) *abs_sum = asum;
   return sum;
 }
 
@@ -258,7 +253,8 @@ __global__ void k_cg_prepare(int64_t n, const double* __restrict__ b, const doub
   }
 }
 
-// r = bw - A x; grid sums (bw, bw) and (r, r). MODE 0: first setup (also sets tol2, zero_rhs and
+// r = bw - A x, row by row in compensated arithmetic (row_residual_dot2); grid sums (bw, bw),
+// (r, r) and the floor's (|A||x| + |bw|)^2. MODE 0: first setup (also sets tol2, zero_rhs and
 // the initial convergence test); MODE 1: true residual at exit (stores (r, r) in aux[0]).
 template <int MASKC, int MODE>
 __global__ void __launch_bounds__(TPB) k_cg_residual(Geom g, const double* __restrict__ val,
@@ -270,11 +266,9 @@ __global__ void __launch_bounds__(TPB) k_cg_residual(Geom g, const double* __res
   for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
     const int col = row / g.nz;
     const int k = row - col * g.nz;
-    bool d = false;
     double asum = 0.0;
-    const double ax = row_dot<MASKC, double, double, MODE == 1>(g, val, x, row, col, k, d, &asum);
     const double bi = bw[row];
-    const double ri = bi - ax;
+    const double ri = row_residual_dot2<MASKC>(g, val, x, bi, row, col, k, asum);
     r[row] = ri;
     v[0] = fma(bi, bi, v[0]);
     v[1] = fma(ri, ri, v[1]);
@@ -1021,7 +1015,8 @@ int pcg_run(pm_operator* op, int which, const double* b, double* x, const pm_sol
   int restarts = 0;
   int first_pass = 0;
   int status = PM_OK;
-  double rel_true = 0.0, rel_floor = 0.0;
+  double rel_true = 0.0, rel_floor = 0.0, prev_true = -1.0;
+  bool accepted = false;
   if (c->sc_host->zero_rhs) {
     k_fill<<<G, TPB, 0, s>>>(x, op->n, 0.0);
     count_launch();
@@ -1046,12 +1041,15 @@ int pcg_run(pm_operator* op, int which, const double* b, double* x, const pm_sol
       if ((st = read_scalars(c, s))) return st;
       rel_true = std::sqrt(c->sc_host->aux[0] / c->sc_host->bb);
       rel_floor = std::ldexp(1.0, -53) * std::sqrt(c->sc_host->aux[1] / c->sc_host->bb);
-      // Accepted when the true residual meets rtol, or when it is already below the floor that
-      // rounding x to FP64 alone produces (backward error at the unit roundoff): restarts could
-      // not lower it further.
-      if (status != PM_OK || rel_true <= std::max(o->rtol, rel_floor) || restarts >= o->max_restarts ||
-          c->sc_host->iter >= o->max_iter)
-        break;
+      // Accepted when the (compensated, hence exact to one rounding) true residual meets rtol,
+      // or when it lies below the floor that rounding x to FP64 alone can cause (backward error
+      // at the unit roundoff) and restarts no longer lower it: the last restart did not halve
+      // it, or no restart is left.
+      const bool stalled = prev_true >= 0.0 && rel_true > 0.5 * prev_true;
+      const bool last = restarts >= o->max_restarts || c->sc_host->iter >= o->max_iter;
+      accepted = rel_true <= o->rtol || (rel_true <= rel_floor && (stalled || last));
+      if (status != PM_OK || accepted || last) break;
+      prev_true = rel_true;
       ++restarts;
       // restart from the true residual held in r
       PcgScalars* hs = c->sc_host;
@@ -1061,7 +1059,7 @@ int pcg_run(pm_operator* op, int which, const double* b, double* x, const pm_sol
       launch_first(op, which, proj, prec, dinv, s);
       if ((st = read_scalars(c, s))) return st;
     }
-    if (status == PM_OK && rel_true > std::max(o->rtol, rel_floor)) status = PM_NOT_CONVERGED;
+    if (status == PM_OK && !accepted) status = PM_NOT_CONVERGED;
   }
   if (proj) {
     // keep m'x = 0 exactly as returned result
@@ -1756,9 +1754,11 @@ int mixed_run(pm_operator* op, int which, const double* b, double* x, const pm_s
       bytes += (double)op->n * (15 * 8 + 3 * 8);
       rel_true = std::sqrt(c->sc_host->aux[0] / bb);
       rel_floor = std::ldexp(1.0, -53) * std::sqrt(c->sc_host->aux[1] / bb);
-      if (rel_true <= std::max(o->rtol, rel_floor)) break;
-      // stagnation: three replacements in a row that did not halve the true residual
-      stalled = rel_true > 0.5 * prev_true ? stalled + 1 : 0;
+      // the refinement step did not halve the (compensated) true residual
+      const bool stalled_now = rel_true > 0.5 * prev_true;
+      if (rel_true <= o->rtol || (rel_true <= rel_floor && stalled_now)) break;
+      // stagnation above the floor: three replacements in a row that did not halve it
+      stalled = stalled_now ? stalled + 1 : 0;
       prev_true = rel_true;
       if (stalled >= 3) {
         status = PM_NOT_CONVERGED;
@@ -1768,8 +1768,8 @@ int mixed_run(pm_operator* op, int which, const double* b, double* x, const pm_s
         status = PM_BREAKDOWN;
         break;
       }
-      if (c->sc_in_host->iter >= o->max_iter) {
-        status = PM_NOT_CONVERGED;
+      if (c->sc_in_host->iter >= o->max_iter) {  // no iteration left: accepted only below the floor
+        status = rel_true <= rel_floor ? PM_OK : PM_NOT_CONVERGED;
         break;
       }
       // residual replacement: r32 = (float)(b - A x); the interrupted step is finished with it
@@ -1829,6 +1829,60 @@ int spmv(pm_operator* op, int which, const double* x, double* y, cudaStream_t s)
   }
   count_launch();
   return cuda_check(cudaGetLastError(), "k_spmv");
+}
+
+namespace {
+// r = b - A x by row_residual_dot2, with the grid sums (r, r), (|A||x| + |b|)^2 and (b, b) left
+// in aux[2..4] of the operator's scalar block (ticket 5).
+template <int MASKC>
+__global__ void __launch_bounds__(TPB) k_residual_any(Geom g, const double* __restrict__ val,
+                                                      const double* __restrict__ b, const double* __restrict__ x,
+                                                      double* __restrict__ r, double* partials, PcgScalars* sc) {
+  double v[3] = {0.0, 0.0, 0.0};
+  const int n = (int)g.n;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
+    const int col = row / g.nz;
+    const int k = row - col * g.nz;
+    double asum = 0.0;
+    const double bi = b[row];
+    const double ri = row_residual_dot2<MASKC>(g, val, x, bi, row, col, k, asum);
+    r[row] = ri;
+    v[0] = fma(ri, ri, v[0]);
+    const double f = asum + fabs(bi);
+    v[1] = fma(f, f, v[1]);
+    v[2] = fma(bi, bi, v[2]);
+  }
+  if (grid_sum<3>(v, partials, &sc->count[5]) && threadIdx.x == 0) {
+    sc->aux[2] = v[0];
+    sc->aux[3] = v[1];
+    sc->aux[4] = v[2];
+  }
+}
+}  // namespace
+
+int residual(pm_operator* op, int which, const double* b, const double* x, double* r, double* norms,
+             cudaStream_t s) {
+  const int vs = which_valset(which);
+  if (vs < 0) return set_error(PM_EINVAL, "unknown operator");
+  int st = ensure_ctx(op);
+  if (st) return st;
+  SolveCtx* c = op->ctx;
+  Geom g = geom_of(op);
+  const int G = grid_for(op->n, TPB, op->num_sms);
+  switch (which_mask(which)) {
+    case 0: k_residual_any<0><<<G, TPB, 0, s>>>(g, op->d_val[vs], b, x, r, c->partials, c->sc); break;
+    case 1: k_residual_any<1><<<G, TPB, 0, s>>>(g, op->d_val[vs], b, x, r, c->partials, c->sc); break;
+    case 2: k_residual_any<2><<<G, TPB, 0, s>>>(g, op->d_val[vs], b, x, r, c->partials, c->sc); break;
+    default: k_residual_any<-1><<<G, TPB, 0, s>>>(g, op->d_val[vs], b, x, r, c->partials, c->sc); break;
+  }
+  count_launch();
+  if ((st = cuda_check(cudaGetLastError(), "k_residual_any"))) return st;
+  if (!norms) return PM_OK;
+  if ((st = read_scalars(c, s))) return st;
+  norms[0] = c->sc_host->aux[2];
+  norms[1] = c->sc_host->aux[3];
+  norms[2] = c->sc_host->aux[4];
+  return PM_OK;
 }
 
 int pcg_solve(pm_operator* op, int which, const double* b, double* x, const pm_solve_opts* o,

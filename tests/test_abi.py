@@ -75,6 +75,12 @@ def test_host_side_validation_without_gpu(lib_path):
     ph_bad = api.Physics((ctypes.c_double * 3)(1, 1, 1), 0.0, None)
     depth[2, 2] = 1.0
     assert lib.pm_assemble_operator(ctypes.byref(d), ctypes.byref(ph_bad), ctypes.byref(h), None) == api.PM_EINVAL
+    # solves and residuals with a null operator or vector
+    nb = (ctypes.c_double * 3)()
+    assert lib.pm_residual(None, api.OP_PRESSURE, None, None, None, nb, None) == api.PM_EINVAL
+    o = api.SolveOpts(1e-8, 100, api.PREC_JACOBI, api.FP64, 0, 3, 0.0)
+    assert lib.pm_pcg_solve_noalloc(None, api.OP_PRESSURE, None, None, ctypes.byref(o), None, None) == api.PM_EINVAL
+    assert lib.pm_pcg_solve(None, api.OP_PRESSURE, None, None, ctypes.byref(o), None, None) == api.PM_EINVAL
 
 
 def test_operator_bytes_scales(lib_path):

@@ -185,6 +185,42 @@ def test_pcg_iterations_and_solution(name, which, prec):
         assert abs(ops.m @ xg) <= 1e-12 * np.abs(xg).max() * ops.m.sum()
 
 
+@pytest.mark.parametrize("name", ["box16", "ocean48"])
+@pytest.mark.parametrize("which", [pm.OP_VEL_U2, pm.OP_VEL1_U3, pm.OP_PRESSURE, pm.OP_MASS, pm.OP_GRAD_Z])
+def test_compensated_residual_is_exact(name, which):
+    """pm_residual at a nearly converged x, where b - A x cancels to 1e-12 of |A||x|: against the
+    residual of the operator the library holds (pm_operator_export) in exact rational arithmetic,
+    row by row to about one rounding of r. The oracle's own matrix differs from the assembled one
+    by up to 1e-12 (summation order), which this cancellation would magnify, so the reference
+    here is exact arithmetic on the stored values, not the oracle."""
+    from fractions import Fraction
+    b, op, ops = case(name)
+    vals, nbr, _ = op.export(which)
+    A = ell_to_csr(vals, nbr, op.nz)
+    x = random_vector(op.n, 31 + which)
+    scale = np.abs(A) @ np.abs(x)
+    rhs = A @ x + 1e-12 * scale * random_vector(op.n, 32)
+    r = torch.empty(op.n, dtype=torch.float64, device="cuda")
+    rr, ff, bb = op.residual(which, dev(rhs), dev(x), r)
+    rg = r.cpu().numpy()
+    rows = np.random.default_rng(33).choice(op.n, size=min(op.n, 600), replace=False)
+    A = A.tocsr()
+    worst_plain = 0.0
+    plain = rhs - A @ x
+    for i in rows:
+        acc = Fraction(float(rhs[i]))
+        for k in range(A.indptr[i], A.indptr[i + 1]):
+            acc -= Fraction(float(A.data[k])) * Fraction(float(x[A.indices[k]]))
+        err = abs(Fraction(float(rg[i])) - acc)
+        assert err <= Fraction(2 * 2.0 ** -53) * abs(acc) + Fraction(1e-30) * Fraction(float(scale[i])), i
+        if acc != 0:
+            worst_plain = max(worst_plain, float(abs(Fraction(float(plain[i])) - acc) / abs(acc)))
+    assert worst_plain > 1e-4          # the plain FP64 residual is off by far more in some row
+    assert rr == pytest.approx(float(rg @ rg), rel=1e-12)
+    assert bb == pytest.approx(float(rhs @ rhs), rel=1e-12)
+    assert ff == pytest.approx(float(np.sum((scale + np.abs(rhs)) ** 2)), rel=1e-10)
+
+
 @pytest.mark.parametrize("which", [pm.OP_VEL_U1, pm.OP_PRESSURE])
 def test_warm_start_and_iteration_cap(which):
     b, op, ops = case("small")
