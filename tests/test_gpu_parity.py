@@ -221,6 +221,50 @@ def test_compensated_residual_is_exact(name, which):
     assert ff == pytest.approx(float(np.sum((scale + np.abs(rhs)) ** 2)), rel=1e-10)
 
 
+def test_pressure_solve_stops_at_the_rounded_exact_solution():
+    """Asked for 1e-11 on the thin ocean basin's pressure system, below what an FP64 vector
+    attains there (about 4e-11), the solve restarts until the exact residual stops halving and is
+    accepted below the FP64 floor, within 1.5x of the FP64 rounding of the exact solution. That
+    rounding comes from double-double refinement (x_hi + x_lo) through the library's own
+    compensated residual and solves."""
+    b, op, ops = case("ocean48")
+    rhs = _rhs(ops, pm.OP_PRESSURE, 61)
+    bc = dev(rhs - (rhs.sum() / ops.m.sum()) * ops.m)
+    x = torch.zeros_like(bc)
+    st = op.solve(pm.OP_PRESSURE, bc, x, pm.Options(rtol=1e-11, prec=pm.PREC_LINE, max_restarts=8))
+    assert st.status == pm.PM_OK and st.rel_residual_floor >= st.rel_residual_true > 1e-11
+    assert st.outer_iters >= 1
+    r = torch.empty_like(bc)
+    bn = float(bc.norm())
+
+    def rel(xh, xl=None):
+        op.residual(pm.OP_PRESSURE, bc, xh, r)
+        out = r.clone()
+        if xl is not None:
+            t = torch.empty_like(xl)
+            op.spmv(pm.OP_PRESSURE, xl, t)
+            out -= t
+        return out, float(out.norm()) / bn
+
+    assert rel(x)[1] == pytest.approx(st.rel_residual_true, rel=1e-9)
+    xh, xl = x.clone(), torch.zeros_like(x)
+    for _ in range(6):
+        res, _ = rel(xh, xl)
+        d = torch.zeros_like(x)
+        op.solve(pm.OP_PRESSURE, res, d, pm.Options(rtol=1e-4, prec=pm.PREC_LINE, max_restarts=0),
+                 allow_not_converged=True)
+        s = xh + d
+        bv = s - xh
+        e = (xh - (s - bv)) + (d - bv)
+        xh, xl = s, xl + e
+        s = xh + xl
+        xl = xl - (s - xh)
+        xh = s
+    assert rel(xh, xl)[1] < 0.05 * st.rel_residual_true     # the pair gets far below any FP64 vector
+    best = rel(xh)[1]                                          # its FP64 rounding
+    assert st.rel_residual_true <= 1.5 * best, (st.rel_residual_true, best)
+
+
 @pytest.mark.parametrize("which", [pm.OP_VEL_U1, pm.OP_PRESSURE])
 def test_warm_start_and_iteration_cap(which):
     b, op, ops = case("small")
