@@ -297,6 +297,35 @@ enum { PM_FIELD_U1 = 0, PM_FIELD_U2 = 1, PM_FIELD_U3 = 2,
        PM_FIELD_P = 6, PM_FIELD_Q = 7, PM_FIELD_UT1 = 8, PM_FIELD_UT2 = 9, PM_FIELD_UT3 = 10,
        PM_FIELD_BP = 11 };
 int pm_state_field(const pm_state* st, int32_t field, double* dst, pm_stream stream);
+/* Set one field (PM_FIELD_U1 .. PM_FIELD_Q) from a caller device vector of length n, and the step
+ * index (0: the next step is the BDF1 start step). With these, a state can be restored exactly
+ * (u^k, u^{k-1}, p^k, the pressure-increment warm start q). Async. */
+int pm_state_set_field(pm_state* st, int32_t field, const double* src, pm_stream stream);
+int pm_state_set_step_index(pm_state* st, int32_t step_index);
+
+/* Checkpoint and resume of a time loop (Section 3's BDF2 recurrence needs u^k and u^{k-1}).
+ * pm_state_save writes u^k (3), u^{k-1} (3), p^k, q and the step index of `st` to `path`: a
+ * 4096-byte ASCII header (one JSON object, space padded, ending in a newline) followed by the
+ * eight fields as little-endian IEEE-754 float64 arrays of n values, in that order. The header
+ * records the format version, n, the grid (nx, ny, nz, ncols, dx, dy), dt, nu, an FNV-1a 64-bit
+ * hash of the ocean column list and of the payload. The file is written under a temporary name
+ * and renamed, so an interrupted save leaves any previous checkpoint intact.
+ * pm_state_load reads such a file into `st`, whose operator must be the same basin (grid, column
+ * list, dt, nu): otherwise, or for a wrong version, size or payload hash, PM_EINVAL and `st` is
+ * unchanged. A state saved and loaded continues bit for bit as the uninterrupted run would.
+ * Both synchronise the stream. Errors: PM_EINVAL, PM_ENOMEM, PM_ECUDA (I/O errors: PM_EINVAL with
+ * the system's message in pm_last_error). */
+int pm_state_save(const pm_state* st, const char* path, pm_stream stream);
+int pm_state_load(pm_state* st, const char* path, pm_stream stream);
+
+/* Diagnostics of the state after a step (no paper counterpart; they monitor the time loop of
+ * Section 3): out[PM_DIAG_KINETIC_ENERGY] = (1/2) sum_c u_c' M u_c, out[PM_DIAG_DIV_U] =
+ * || sum_c G_c u_c ||_2 (the integral of div u^k against every basis function; the correction of
+ * Eq. correc_velo_u exists to make it small), out[PM_DIAG_DIV_UT] = the same for the last
+ * prediction u~, out[PM_DIAG_P_MEAN] = m'p / 1'm. Synchronises the stream. */
+enum { PM_DIAG_KINETIC_ENERGY = 0, PM_DIAG_DIV_U = 1, PM_DIAG_DIV_UT = 2, PM_DIAG_P_MEAN = 3,
+       PM_DIAG_COUNT = 4 };
+int pm_state_diagnostics(pm_operator* op, const pm_state* st, double* out, pm_stream stream);
 
 enum { PM_STEP_LUMPED = 0, PM_STEP_CONSISTENT = 1 };
 

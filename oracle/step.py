@@ -122,6 +122,17 @@ def discrete_divergence(ops: fem.Operators, u: np.ndarray) -> np.ndarray:
     return sum(ops.G[c] @ u[c] for c in range(3))
 
 
+def diagnostics(ops: fem.Operators, st: State, u_tilde: Optional[np.ndarray] = None) -> dict:
+    """Monitors of the time loop (no paper counterpart): kinetic energy (1/2) sum_c u_c' M u_c,
+    ||sum_c G_c u_c||_2 for u^k and for the last prediction u~ (the quantity the correction of
+    Eq. correc_velo_u reduces), and the mean pressure m'p / 1'm."""
+    ut = np.zeros_like(st.u) if u_tilde is None else u_tilde
+    return {"kinetic_energy": 0.5 * float(sum(st.u[c] @ (ops.M @ st.u[c]) for c in range(3))),
+            "div_u": float(np.linalg.norm(discrete_divergence(ops, st.u))),
+            "div_u_tilde": float(np.linalg.norm(discrete_divergence(ops, ut))),
+            "p_mean": float(ops.m @ st.p) / float(ops.m.sum())}
+
+
 def project_step(ops: fem.Operators, st: State, opts: StepOptions = StepOptions()) -> StepReport:
     mesh = ops.mesh
     bdf1 = st.step == 0

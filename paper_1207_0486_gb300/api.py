@@ -26,6 +26,8 @@ FP64, FP32_REFINE, BF16_REFINE = 0, 1, 2
 STEP_LUMPED, STEP_CONSISTENT = 0, 1
 (FIELD_U1, FIELD_U2, FIELD_U3, FIELD_U1_PREV, FIELD_U2_PREV, FIELD_U3_PREV, FIELD_P, FIELD_Q,
  FIELD_UT1, FIELD_UT2, FIELD_UT3, FIELD_BP) = range(12)
+DIAG_KINETIC_ENERGY, DIAG_DIV_U, DIAG_DIV_UT, DIAG_P_MEAN, DIAG_COUNT = range(5)
+DIAG_NAMES = ("kinetic_energy", "div_u", "div_u_tilde", "p_mean")
 
 # Slot offsets (di, dj, dk) of the 15-slot layout, in slot order (documented in pm.h's layout).
 SLOT_OFFSETS = [(0, 0, -1), (0, 0, 0), (0, 0, 1), (1, 0, 0), (1, 0, 1), (-1, 0, -1), (-1, 0, 0),
@@ -84,6 +86,11 @@ SIGNATURES = {
     "pm_state_set": (_I, [_P, _P, _P, _P, _P, ctypes.c_int32, _P]),
     "pm_state_step_index": (ctypes.c_int32, [_P]),
     "pm_state_field": (_I, [_P, ctypes.c_int32, _P, _P]),
+    "pm_state_set_field": (_I, [_P, ctypes.c_int32, _P, _P]),
+    "pm_state_set_step_index": (_I, [_P, ctypes.c_int32]),
+    "pm_state_save": (_I, [_P, ctypes.c_char_p, _P]),
+    "pm_state_load": (_I, [_P, ctypes.c_char_p, _P]),
+    "pm_state_diagnostics": (_I, [_P, _P, _P, _P]),
     "pm_project_step": (_I, [_P, _P, _P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveOpts),
                              ctypes.c_int32, _P, _P]),
     "pm_operator_destroy": (None, [_P]),
@@ -333,6 +340,40 @@ class State:
         out = torch.empty(self.op.n, dtype=torch.float64, device="cuda") if out is None else out
         _check(load().pm_state_field(self.handle, which, _dptr(out, self.op.n, "out"), _stream(stream)), "state_field")
         return out
+
+    def set_field(self, which: int, src, stream=None):
+        """pm_state_set_field: u^k, u^{k-1}, p or q (FIELD_U1 .. FIELD_Q) from a CUDA float64 tensor."""
+        _check(load().pm_state_set_field(self.handle, which, _dptr(src, self.op.n, "src"), _stream(stream)),
+               "state_set_field")
+
+    def set_step_index(self, k: int):
+        _check(load().pm_state_set_step_index(self.handle, k), "state_set_step_index")
+
+    def snapshot(self, stream=None):
+        """Device copies of the fields that define the time loop (u^k, u^{k-1}, p, q) and the step
+        index; restore() puts them back (the in-memory counterpart of save / load)."""
+        return [self.field(f, stream=stream) for f in range(FIELD_Q + 1)], self.step_index
+
+    def restore(self, snap, stream=None):
+        fields, k = snap
+        for f, t in enumerate(fields):
+            self.set_field(f, t, stream)
+        self.set_step_index(k)
+
+    def save(self, path: str, stream=None):
+        """pm_state_save: checkpoint file (header + little-endian float64 fields)."""
+        _check(load().pm_state_save(self.handle, os.fsencode(path), _stream(stream)), "state_save")
+
+    def load_checkpoint(self, path: str, stream=None):
+        """pm_state_load: resume from a checkpoint written by save() for the same basin."""
+        _check(load().pm_state_load(self.handle, os.fsencode(path), _stream(stream)), "state_load")
+
+    def diagnostics(self, stream=None) -> dict:
+        """pm_state_diagnostics: kinetic energy, discrete divergences of u^k and of the last
+        prediction, mean pressure."""
+        out = (ctypes.c_double * DIAG_COUNT)()
+        _check(load().pm_state_diagnostics(self.op.handle, self.handle, out, _stream(stream)), "state_diagnostics")
+        return {name: out[i] for i, name in enumerate(DIAG_NAMES)}
 
     def set(self, u1=None, u2=None, u3=None, p=None, step_index=0, stream=None):
         _check(load().pm_state_set(self.handle, _dptr(u1), _dptr(u2), _dptr(u3), _dptr(p),

@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpm_gb300.so")
 SOURCES = ["pm_api.cu", "pm_mesh.cu", "pm_assemble.cu", "pm_solve.cu", "pm_step.cu", "pm_noalloc.cu",
-           "pm_batch.cu"]
+           "pm_batch.cu", "pm_checkpoint.cu"]
 # The persistent batched kernel reads data other blocks write during the launch: plain global
 # loads in that file are cached in L2 only (ld.global.cg), never in the non-coherent L1.
 EXTRA = {"pm_batch.cu": ["-Xptxas", "-dlcm=cg"]}

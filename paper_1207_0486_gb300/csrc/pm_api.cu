@@ -311,6 +311,11 @@ int pm_state_create(pm_operator* op, pm_state** out) {
       return cuda_check(e, "state allocation");
     }
   }
+  cudaError_t e = cudaMalloc((void**)&st->diag, ((size_t)PM_DIAG_COUNT * MAX_GRID + PM_DIAG_COUNT) * sizeof(double));
+  if (e != cudaSuccess) {
+    pm_state_destroy(st);
+    return cuda_check(e, "state allocation");
+  }
   *out = st;
   return PM_OK;
 }
@@ -343,6 +348,31 @@ int pm_state_field(const pm_state* st, int32_t field, double* dst, pm_stream str
   }
   return cuda_check(cudaMemcpyAsync(dst, src, st->op->n * sizeof(double), cudaMemcpyDeviceToDevice,
                                     (cudaStream_t)stream), "state field");
+}
+
+int pm_state_set_field(pm_state* st, int32_t field, const double* src, pm_stream stream) {
+  if (!st || !src) return set_error(PM_EINVAL, "null argument");
+  double* dst = nullptr;
+  switch (field) {
+    case PM_FIELD_U1: case PM_FIELD_U2: case PM_FIELD_U3: dst = st->u[field - PM_FIELD_U1]; break;
+    case PM_FIELD_U1_PREV: case PM_FIELD_U2_PREV: case PM_FIELD_U3_PREV: dst = st->u_prev[field - PM_FIELD_U1_PREV]; break;
+    case PM_FIELD_P: dst = st->p; break;
+    case PM_FIELD_Q: dst = st->q; break;
+    default: return set_error(PM_EINVAL, "only u^k, u^{k-1}, p and q can be set");
+  }
+  return cuda_check(cudaMemcpyAsync(dst, src, st->op->n * sizeof(double), cudaMemcpyDeviceToDevice,
+                                    (cudaStream_t)stream), "state set field");
+}
+
+int pm_state_set_step_index(pm_state* st, int32_t step_index) {
+  if (!st || step_index < 0) return set_error(PM_EINVAL, "bad argument");
+  st->step = step_index;
+  return PM_OK;
+}
+
+int pm_state_diagnostics(pm_operator* op, const pm_state* st, double* out, pm_stream stream) {
+  if (!op || !st || !out || st->op != op) return set_error(PM_EINVAL, "bad argument");
+  return step_diagnostics(op, st, out, (cudaStream_t)stream);
 }
 
 int pm_state_set(pm_state* st, const double* u1, const double* u2, const double* u3, const double* p,
@@ -385,6 +415,7 @@ void pm_state_destroy(pm_state* st) {
   double* fields[] = {st->u[0], st->u[1], st->u[2], st->u_prev[0], st->u_prev[1], st->u_prev[2],
                       st->p, st->q, st->ut[0], st->ut[1], st->ut[2], st->b[0], st->b[1], st->b[2], st->bp};
   for (double* f : fields) cudaFree(f);
+  cudaFree(st->diag);
   delete st;
 }
 

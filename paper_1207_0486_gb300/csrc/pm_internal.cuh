@@ -239,6 +239,7 @@ struct pm_state {
   double* ut[3];    // u~ (prediction)
   double* b[3];     // velocity right-hand sides
   double* bp;       // pressure right-hand side
+  double* diag;     // diagnostics partials: PM_DIAG_COUNT lanes x MAX_GRID blocks, then the totals
   int32_t step;
 };
 
@@ -278,6 +279,7 @@ int pcg_solve(pm_operator* op, int which, const double* b, double* x, const pm_s
 void destroy_ctx(pm_operator* op);
 
 // pm_step.cu
+int step_diagnostics(pm_operator* op, const pm_state* st, double* out, cudaStream_t s);
 int project_step(pm_operator* op, pm_state* st, const double* th1, const double* th2,
                  const pm_solve_opts* vel, const pm_solve_opts* pres, int correction,
                  pm_solve_stats* stats, cudaStream_t s);

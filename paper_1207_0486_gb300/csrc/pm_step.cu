@@ -12,6 +12,7 @@
 //                 end of Section 3 would add the gradient the correction exists to remove.
 //   k_axpy        p^{k+1} = p^k + q (Eq. fofa_pres_cor_h: the L2 projection onto P_h is the
 //                 identity for q, p^k in P_h)
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 
@@ -306,7 +307,95 @@ int grid_for(int64_t n, int threads, int sms) {
   return (int)gsz;
 }
 
+// Diagnostics of a state, per row i: u_c,i (M u_c)_i for the kinetic energy, the discrete
+// divergences (sum_c G_c u_c)_i of u^k and (sum_c G_c u~_c)_i of the last prediction, and m_i p_i.
+// Each block writes its partial sums (lane-major, PM_DIAG_COUNT lanes); k_diag_total adds them in
+// block order (deterministic).
+__global__ void __launch_bounds__(TPB) k_diagnostics(Geom g, const double* __restrict__ mval,
+                                                     const double* __restrict__ gv0, const double* __restrict__ gv1,
+                                                     const double* __restrict__ gv2, StepIn u, StepIn ut,
+                                                     const double* __restrict__ m, const double* __restrict__ p,
+                                                     double* __restrict__ part) {
+  const int nz = g.nz;
+  double acc[PM_DIAG_COUNT] = {0.0, 0.0, 0.0, 0.0};
+  const double* gv[3] = {gv0, gv1, gv2};
+  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < g.n;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    const int col = (int)(row / nz);
+    const int k = (int)(row - (int64_t)col * nz);
+    int nb[NNBR];
+#pragma unroll
+    for (int q = 0; q < NNBR; ++q) nb[q] = q == 0 ? col : g.nbr[(int64_t)col * NNBR + q];
+    double mu[3] = {0, 0, 0}, du = 0.0, dut = 0.0;
+#pragma unroll
+    for (int sl = 0; sl < NSLOT; ++sl) {
+      const int q = slot_q(sl);
+      const int kk = k + slot_dk(sl);
+      if (nb[q] < 0 || kk < 0 || kk >= nz) continue;
+      const int64_t j = (int64_t)nb[q] * nz + kk;
+      const double mv = mval[(int64_t)sl * g.npad + row];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const double gcv = gv[c][(int64_t)sl * g.npad + row];
+        mu[c] = fma(mv, u.u[c][j], mu[c]);
+        du = fma(gcv, u.u[c][j], du);
+        dut = fma(gcv, ut.u[c][j], dut);
+      }
+    }
+    double e = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) e = fma(u.u[c][row], mu[c], e);
+    acc[PM_DIAG_KINETIC_ENERGY] += 0.5 * e;
+    acc[PM_DIAG_DIV_U] = fma(du, du, acc[PM_DIAG_DIV_U]);
+    acc[PM_DIAG_DIV_UT] = fma(dut, dut, acc[PM_DIAG_DIV_UT]);
+    acc[PM_DIAG_P_MEAN] = fma(m[row], p[row], acc[PM_DIAG_P_MEAN]);
+  }
+  __shared__ double sm[PM_DIAG_COUNT][TPB / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int l = 0; l < PM_DIAG_COUNT; ++l) {
+    double v = acc[l];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sm[l][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < PM_DIAG_COUNT) {
+    double v = 0.0;
+    for (int w = 0; w < TPB / 32; ++w) v += sm[threadIdx.x][w];
+    part[(int64_t)threadIdx.x * MAX_GRID + blockIdx.x] = v;
+  }
+}
+
+// One block: totals of the block partials, in block order; the two divergences as 2-norms and the
+// mean pressure m'p / 1'm.
+__global__ void k_diag_total(const double* __restrict__ part, int nblocks, double one_m, double* __restrict__ out) {
+  if (threadIdx.x >= PM_DIAG_COUNT) return;
+  double v = 0.0;
+  for (int b = 0; b < nblocks; ++b) v += part[(int64_t)threadIdx.x * MAX_GRID + b];
+  if (threadIdx.x == PM_DIAG_DIV_U || threadIdx.x == PM_DIAG_DIV_UT) v = sqrt(v);
+  if (threadIdx.x == PM_DIAG_P_MEAN) v /= one_m;
+  out[threadIdx.x] = v;
+}
+
 }  // namespace
+
+int step_diagnostics(pm_operator* op, const pm_state* st, double* out, cudaStream_t s) {
+  Geom g = geom_of(op);
+  const int G = std::min(grid_for(op->n, TPB, op->num_sms), MAX_GRID);
+  StepIn u, ut;
+  for (int c = 0; c < 3; ++c) {
+    u.u[c] = st->u[c];
+    ut.u[c] = st->ut[c];
+  }
+  k_diagnostics<<<G, TPB, 0, s>>>(g, op->d_val[VS_M], op->d_val[VS_G0], op->d_val[VS_G1], op->d_val[VS_G2], u, ut,
+                                  op->d_m, st->p, st->diag);
+  double* tot = st->diag + (int64_t)PM_DIAG_COUNT * MAX_GRID;
+  k_diag_total<<<1, 32, 0, s>>>(st->diag, G, op->one_m, tot);
+  count_launch(2);
+  int r = cuda_check(cudaMemcpyAsync(out, tot, PM_DIAG_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s), "diagnostics");
+  if (!r) r = cuda_check(cudaStreamSynchronize(s), "diagnostics");
+  return r;
+}
 
 int project_step(pm_operator* op, pm_state* st, const double* th1, const double* th2,
                  const pm_solve_opts* vel, const pm_solve_opts* pres, int correction,

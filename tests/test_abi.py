@@ -81,6 +81,13 @@ def test_host_side_validation_without_gpu(lib_path):
     o = api.SolveOpts(1e-8, 100, api.PREC_JACOBI, api.FP64, 0, 3, 0.0)
     assert lib.pm_pcg_solve_noalloc(None, api.OP_PRESSURE, None, None, ctypes.byref(o), None, None) == api.PM_EINVAL
     assert lib.pm_pcg_solve(None, api.OP_PRESSURE, None, None, ctypes.byref(o), None, None) == api.PM_EINVAL
+    # state fields, checkpoints and diagnostics without a state
+    assert lib.pm_state_field(None, api.FIELD_U1, None, None) == api.PM_EINVAL
+    assert lib.pm_state_set_field(None, api.FIELD_U1, None, None) == api.PM_EINVAL
+    assert lib.pm_state_set_step_index(None, 3) == api.PM_EINVAL
+    assert lib.pm_state_save(None, b"/nonexistent/x.pmck", None) == api.PM_EINVAL
+    assert lib.pm_state_load(None, b"/nonexistent/x.pmck", None) == api.PM_EINVAL
+    assert lib.pm_state_diagnostics(None, None, nb, None) == api.PM_EINVAL
 
 
 def test_operator_bytes_scales(lib_path):

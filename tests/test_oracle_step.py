@@ -88,3 +88,22 @@ def test_correction_lowers_the_discrete_divergence(lumped):
     d_pred = np.linalg.norm(step.discrete_divergence(ops, rep.u_tilde))
     d_corr = np.linalg.norm(step.discrete_divergence(ops, st.u))
     assert d_corr < 0.6 * d_pred, (d_corr, d_pred)
+
+
+def test_diagnostics_closed_forms():
+    """Kinetic energy of a uniform flow is |U|^2 |Omega| / 2 (|Omega| = 1 x 1 x eps for the box);
+    a linear field (x, y, -2z) is divergence free and G_c X_d = delta_cd M 1 makes its discrete
+    divergence vanish; (x, 0, 0) has sum_c G_c u_c = M 1; a constant pressure is its own mean."""
+    b = box_basin(nh=7, nz=5, eps=0.01)
+    ops = fem.assemble(b)
+    st = step.initial_state(ops.n)
+    st.u[0], st.u[1], st.u[2] = 0.3, -0.4, 1.2
+    st.p[:] = 2.5
+    d = step.diagnostics(ops, st)
+    assert d["kinetic_energy"] == pytest.approx(0.5 * (0.09 + 0.16 + 1.44) * 0.01, rel=1e-12, abs=0)
+    assert d["p_mean"] == pytest.approx(2.5, rel=1e-14, abs=0)
+    x, y, z = ops.mesh.xyz.T
+    st.u = np.stack([x, y, -2.0 * z])
+    d = step.diagnostics(ops, st, u_tilde=np.stack([x, 0 * x, 0 * x]))
+    assert d["div_u"] <= 1e-13 * np.linalg.norm(ops.m)
+    assert d["div_u_tilde"] == pytest.approx(np.linalg.norm(ops.m), rel=1e-12, abs=0)
