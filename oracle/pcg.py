@@ -80,31 +80,52 @@ def two_product(a, b):
     return p, al * bl - (((p - ah * bh) - al * bh) - ah * bl)
 
 
+def _padded_rows(A: sp.csr_matrix):
+    """A's rows as (width, n) arrays of values and column indices, each row's entries in stored
+    order and padded with zeros (a zero term changes neither TwoProduct nor TwoSum). Cached on
+    the matrix object."""
+    cached = getattr(A, "_dot2_rows", None)
+    if cached is not None:
+        return cached
+    n = A.shape[0]
+    cnt = np.diff(A.indptr)
+    width = int(cnt.max()) if n else 0
+    rows = np.repeat(np.arange(n), cnt)
+    pos = np.arange(len(A.indices)) - A.indptr[rows]
+    V = np.zeros((width, n))
+    J = np.tile(np.arange(n), (width, 1))
+    V[pos, rows] = A.data
+    J[pos, rows] = A.indices
+    A._dot2_rows = (V, J)
+    return V, J
+
+
 def residual_dot2(A: sp.csr_matrix, x: np.ndarray, b: np.ndarray) -> np.ndarray:
     """r = b - A x with Dot2 per row: the sum b_i - sum_j a_ij x_j is formed from the exact
     products (TwoProduct) by TwoSum, and the errors of both are accumulated and added at the
     end. Vectorised over rows, the terms of a row taken in stored (column) order."""
     A = A.tocsr()
-    n = A.shape[0]
-    cnt = np.diff(A.indptr)
-    rows = np.repeat(np.arange(n), cnt)
-    pos = np.arange(len(A.indices)) - A.indptr[rows]
+    V, J = _padded_rows(A)
     s = np.array(b, dtype=np.float64, copy=True)
-    c = np.zeros(n)
-    for k in range(int(cnt.max()) if n else 0):
-        sel = pos == k
-        r_k = rows[sel]
-        p, e = two_product(A.data[sel], x[A.indices[sel]])
-        t, q = two_sum(s[r_k], -p)
-        s[r_k] = t
-        c[r_k] += q - e
+    c = np.zeros(len(s))
+    for k in range(V.shape[0]):
+        p, e = two_product(V[k], x[J[k]])
+        s, q = two_sum(s, -p)
+        c += q - e
     return s + c
 
 
 def residual_floor(A: sp.spmatrix, x: np.ndarray, b: np.ndarray) -> float:
     """u || |A||x| + |b| ||_2 / ||b||_2 with u = 2^-53: the relative residual that rounding x (and
     b) to FP64 alone can cause, row by row u (|A||x| + |b|)_i."""
-    return 2.0 ** -53 * float(np.linalg.norm(abs(A) @ np.abs(x) + np.abs(b))) / float(np.linalg.norm(b))
+    absA = getattr(A, "_abs", None)
+    if absA is None:
+        absA = abs(A)
+        try:
+            A._abs = absA
+        except AttributeError:
+            pass
+    return 2.0 ** -53 * float(np.linalg.norm(absA @ np.abs(x) + np.abs(b))) / float(np.linalg.norm(b))
 
 
 @dataclass
