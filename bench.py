@@ -132,9 +132,9 @@ def oracle_window_basin():
 
 def oracle_step_bytes(n, rep):
     """Algorithmic PCG bytes of a step, the same per-row model as the GPU path."""
-    per_jac = 15 * 8 + 8 + 8 + 5 * 8 + 2 * 8 + 3 * 8 + 8
-    per_ic0 = per_jac + 2 * 8 * 8 + 4 * 8
-    per_line = per_jac + 8 + 3 * 8 + 8
+    spmv = 15 * 8 + 8 + 8
+    per_ic0 = spmv + 48 + 2 * 8 * 8 + 4 * 8 + 16 + 24
+    per_line = spmv + 48 + 3 * 8 + 8 + 24 + 8      # pressure: m'z adds m
     its_vel = sum(r.iters for r in rep.vel)
     return n * (its_vel * per_ic0 + rep.pres.iters * per_line)
 
@@ -221,7 +221,8 @@ def roofline_of(kt, n, steps, ms_total, peak, peak_kind, sm_mhz=None):
         1: n * (4 * 8 + 2 * 8),             # IC0 path update: x, r, p, w read; x, r written
         2: n * (3 * 8 + 8) / 2,             # (r, z) dot + p update, two launches
         3: n * (2 * 8 * 8 + 4 * 8) / 16,    # IC0 colour phase: F (8 per row per sweep), r / y / z
-        4: n * (2 * 8 + 2 * 8 + 8 + 8 + 3 * 8 + 8 + 8 + 8),  # fused update + line solve
+        4: n * (2 * 8 + 2 * 8 + 8 + 8 + 3 * 8 + 8 + 8),      # fused update + line solve: x, r r/w; p, w,
+                                                              # 3 factors, m read; z written
     }
     spmv_flops = 2 * 16 * n                 # 15 slot FMAs and the (p, Ap) FMA per row
     live = {k: v for k, v in kt.items() if v[1] > 0}
@@ -636,10 +637,11 @@ def run_ours(args):
                             "per_field_max_rel_err_vs_fp64": {k: float(f"{v:.3e}") for k, v in errs.items()}}
 
     small = None
-    try:
-        small = run_small_leg()
-    except Exception as ex:  # reported, never fatal for the headline number
-        small = {"error": str(ex)[:300]}
+    if not args.no_small:
+        try:
+            small = run_small_leg()
+        except Exception as ex:  # reported, never fatal for the headline number
+            small = {"error": str(ex)[:300]}
     batched = None
     if not args.no_batch:
         try:
@@ -731,6 +733,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--cpu-worker", action="store_true")
     ap.add_argument("--nx", type=int, default=512,

@@ -682,7 +682,142 @@ __global__ void __launch_bounds__(LINE_FTPB) k_update_line(Geom g, const double*
   }
 }
 
+// The same fused iteration for 32-level columns, organised by warp instead of by block. A warp
+// task is TCOLS whole columns (TCOLS * 32 consecutive rows, since node id = column * 32 + k):
+//   A (all lanes, coalesced): x += alpha p, r -= alpha w for level k = lane of each column, r
+//     staged into the warp's own shared-memory tile [column][level];
+//   B (lane = column): the Thomas sweep down and up the column in that tile;
+//   C (all lanes, coalesced): z written, m'z.
+// Warps never wait for one another (only __syncwarp), so one warp's sequential sweep overlaps
+// other warps' streaming. (r, z) comes out of the sweep without reading r again: with the factors
+// T = L U of the column block (L lower bidiagonal, diagonal 1/w_k, sub-diagonal lo_k; U unit
+// upper bidiagonal, cp_k), a symmetric T has U = diag(w) L^T, so with t_k = r_k - lo_k y_{k-1},
+// y_k = t_k w_k and z = U^{-1} y,  (r, z) = y' diag(1/w) y = sum_k t_k y_k.
+constexpr int LINE_WNZ = 32;
+template <int PROJ, int TCOLS>
+__global__ void __launch_bounds__(256, 3) k_update_line_w(Geom g, const double* __restrict__ F, double* __restrict__ x,
+                                                     double* __restrict__ r, const double* __restrict__ p,
+                                                     const double* __restrict__ w, double* __restrict__ z,
+                                                     const double* __restrict__ m, double* partials, PcgScalars* sc) {
+  constexpr int NZ = LINE_WNZ, LD = NZ + 1;
+  extern __shared__ double smem[];
+  if (sc_done(sc)) return;
+  const double alpha = sc->alpha;
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  double* ws = smem + wib * (TCOLS * LD);
+  const int ncols = g.ncols;
+  const int n = (int)g.n;
+  const int ntask = (ncols + TCOLS - 1) / TCOLS;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  double v[4] = {0.0, 0.0, 0.0, 0.0};   // (r, r), (r, z), m'z, 1'r
+  for (int t = blockIdx.x * (blockDim.x >> 5) + wib; t < ntask; t += nwarps) {
+    const int c0 = t * TCOLS;
+    const int cc = min(TCOLS, ncols - c0);
+    const int row0 = c0 * NZ + lane;
+#pragma unroll 8
+    for (int j = 0; j < cc; ++j) {
+      const int row = row0 + j * NZ;
+      x[row] = fma(alpha, p[row], x[row]);
+      const double ri = fma(-alpha, w[row], r[row]);
+      r[row] = ri;
+      ws[j * LD + lane] = ri;
+      v[0] = fma(ri, ri, v[0]);
+      if (PROJ) v[3] += ri;
+    }
+    __syncwarp();
+    if (lane < cc) {
+      const int col = c0 + lane;
+      double* cs = ws + lane * LD;
+      double y = 0.0, rz = 0.0;
+#pragma unroll 8
+      for (int k = 0; k < NZ; ++k) {
+        const int li = k * ncols + col;
+        const double tk = fma(-F[li], y, cs[k]);
+        y = tk * F[n + li];
+        rz = fma(tk, y, rz);
+        cs[k] = y;
+      }
+      double zn = y;
+#pragma unroll 8
+      for (int k = NZ - 2; k >= 0; --k) {
+        const int li = k * ncols + col;
+        zn = fma(-F[2 * n + li], zn, cs[k]);
+        cs[k] = zn;
+      }
+      v[1] += rz;
+    }
+    __syncwarp();
+#pragma unroll 8
+    for (int j = 0; j < cc; ++j) {
+      const int row = row0 + j * NZ;
+      const double zi = ws[j * LD + lane];
+      z[row] = zi;
+      if (PROJ) v[2] = fma(m[row], zi, v[2]);
+    }
+    __syncwarp();
+  }
+  if (grid_sum<4>(v, partials, &sc->count[4]) && threadIdx.x == 0) {
+    sc->iter += 1;
+    sc->rr = v[0];
+    if (v[0] <= sc->tol2) {
+      sc->done = 1;
+    } else if (sc->iter >= sc->max_iter) {
+      sc->status = PM_NOT_CONVERGED;
+      sc->done = 1;
+    } else {
+      const double c = PROJ ? v[2] / sc->one_m : 0.0;
+      const double rho_new = v[1] - c * v[3];
+      sc->proj_c = c;
+      sc->beta = rho_new / sc->rho;
+      sc->rho = rho_new;
+      if (!(rho_new > 0.0) || !isfinite(rho_new)) {
+        sc->status = PM_BREAKDOWN;
+        sc->done = 1;
+      }
+    }
+  }
+}
+
+#ifndef PM_LINE_WCOLS
+#define PM_LINE_WCOLS 32
+#endif
+constexpr int LINE_WCOLS = PM_LINE_WCOLS;   // columns per warp task
+constexpr int LINE_WTPB = 256;              // 8 warps per block
+
+// Launch of k_update_line_w: as many warps as make the tasks an equal count per warp, within the
+// kernel's residency and the partials buffer (4 lanes per block).
+void update_line_w(pm_operator* op, int which, bool proj, double* x, cudaStream_t s) {
+  SolveCtx* c = op->ctx;
+  Geom g = geom_of(op);
+  const size_t smem = (size_t)(LINE_WTPB / 32) * LINE_WCOLS * (LINE_WNZ + 1) * sizeof(double);
+  static int slots = 0;
+  if (!slots) {
+    cudaFuncSetAttribute(k_update_line_w<0, LINE_WCOLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_update_line_w<1, LINE_WCOLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_line_w<1, LINE_WCOLS>, LINE_WTPB, smem);
+    slots = std::max(1, per_sm) * op->num_sms;
+  }
+  const int64_t ntask = (op->ncols + LINE_WCOLS - 1) / LINE_WCOLS;
+  const int64_t max_blocks = std::min<int64_t>(slots, (int64_t)NPART * MAX_GRID / 4);
+  const int64_t wpb = LINE_WTPB / 32;
+  const int64_t per_warp = std::max<int64_t>(1, (ntask + max_blocks * wpb - 1) / (max_blocks * wpb));
+  const int64_t warps = (ntask + per_warp - 1) / per_warp;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(max_blocks, (warps + wpb - 1) / wpb));
+  const double* F = op->d_line[which];
+  if (proj)
+    k_update_line_w<1, LINE_WCOLS><<<grid, LINE_WTPB, smem, s>>>(g, F, x, c->r, c->p, c->w, c->z, op->d_m, c->partials, c->sc);
+  else
+    k_update_line_w<0, LINE_WCOLS><<<grid, LINE_WTPB, smem, s>>>(g, F, x, c->r, c->p, c->w, c->z, op->d_m, c->partials, c->sc);
+  count_launch();
+}
+
 void update_line(pm_operator* op, int which, bool proj, double* x, cudaStream_t s) {
+  if (op->nz == LINE_WNZ) {
+    update_line_w(op, which, proj, x, s);
+    return;
+  }
   SolveCtx* c = op->ctx;
   Geom g = geom_of(op);
   const size_t smem = (size_t)LINE_FCOLS * (op->nz + 1) * sizeof(double);
@@ -945,15 +1080,21 @@ int read_scalars(SolveCtx* c, cudaStream_t s) {
   return st;
 }
 
-// Algorithmic bytes of one PCG iteration per row (FP64): SpMV 15 values + p read + w write,
-// update x, r read/write + p, w, dinv read, p-update r, dinv, p read + p write.
-// IC0 adds the factor (8 slots read per row per sweep, two sweeps) and r / y / z traffic;
-// LINE adds r read, 3 factors, z write (its (r, z) reduction is fused).
-double bytes_per_iter(const pm_operator* op, int prec) {
+// Algorithmic bytes of one PCG iteration per row (FP64), each array once per pass:
+//   SpMV: 15 values + p read + w write = 136;
+//   Jacobi: update x, r read/write + p, w, dinv read (z = dinv r inline) = 56, p-update r, dinv,
+//           p read + p write = 32;
+//   IC0: update x, r read/write + p, w read = 48, the factor (8 of its 15 slots per row in each
+//        sweep direction) 128 and r, y, z traffic 32, the (r, z) pass 16, p-update z, p, p = 24;
+//   LINE: update 48, the three line factors and the z write 32 (fused with the update), p-update 24.
+// The pressure adds m (8) where m'z is taken.
+double bytes_per_iter(const pm_operator* op, int prec, bool proj) {
   const double n = (double)op->n;
-  double b = n * (15 * 8 + 8 + 8) + n * (5 * 8 + 2 * 8) + n * (3 * 8 + 8);
-  if (prec == PM_PREC_IC0) b += n * (2 * 8 * 8 + 4 * 8);
-  if (prec == PM_PREC_LINE) b += n * (8 + 3 * 8 + 8);
+  double b = n * (15 * 8 + 8 + 8);
+  if (prec == PM_PREC_IC0) b += n * (48 + 2 * 8 * 8 + 4 * 8 + 16 + 24);
+  else if (prec == PM_PREC_LINE) b += n * (48 + 3 * 8 + 8 + 24);
+  else b += n * (56 + 32);
+  if (proj) b += n * 8;
   return b;
 }
 
@@ -1077,7 +1218,7 @@ int pcg_run(pm_operator* op, int which, const double* b, double* x, const pm_sol
     stats->status = status;
     stats->rel_residual_true = h->zero_rhs ? 0.0 : rel_true;
     stats->rel_residual_rec = h->zero_rhs ? 0.0 : std::sqrt(h->rr / h->bb);
-    stats->bytes_moved = h->iter * bytes_per_iter(op, prec);
+    stats->bytes_moved = h->iter * bytes_per_iter(op, prec, proj);
     stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   if ((st = cuda_check(cudaGetLastError(), "pcg kernels"))) return st;
