@@ -22,6 +22,7 @@ def basin_cases():
         "box16": lambda: theta_basin(box_basin()),
         "small": lambda: small_basin(),
         "ocean48": lambda: ocean_basin(nx=48, ny=40, nz=9, dx=1e5),
+        "ocean32": lambda: ocean_basin(nx=40, ny=36, nz=32, dx=1e5),   # 32 levels: warp-task line kernel
         "box2": lambda: box_basin(nh=2, nz=2),
     }
 
@@ -145,7 +146,7 @@ def _tolerances(name, which):
     sides solve to attainable tolerances and the solution bar is the conditioning bound
     |dx| / |x| <= kappa_eff * residual, about 1e-5 here; everywhere else the bar is 1e-9.
     """
-    if name == "ocean48" and which == pm.OP_PRESSURE:
+    if name.startswith("ocean") and which == pm.OP_PRESSURE:
         return 1e-8, 2e-9, 1e-5
     return 1e-10, (1e-12 if which == pm.OP_PRESSURE else 1e-13), 1e-9
 
@@ -153,6 +154,16 @@ def _tolerances(name, which):
 @pytest.mark.parametrize("name", ["box16", "small", "ocean48"])
 @pytest.mark.parametrize("which,prec", SOLVE_CASES)
 def test_pcg_iterations_and_solution(name, which, prec):
+    _check_solve(name, which, prec)
+
+
+@pytest.mark.parametrize("which", [pm.OP_VEL_U1, pm.OP_VEL1_U3, pm.OP_PRESSURE])
+def test_line_solves_on_32_level_columns(which):
+    """32-level columns take the warp-task fused line kernel (others the block kernel)."""
+    _check_solve("ocean32", which, pm.PREC_LINE)
+
+
+def _check_solve(name, which, prec):
     b, op, ops = case(name)
     rhs = _rhs(ops, which, 17 + which)
     bd = dev(rhs)
@@ -306,7 +317,7 @@ def test_bad_arguments_raise():
         op.solve(pm.OP_GRAD_X, xd, xd)
 
 
-@pytest.mark.parametrize("name", ["box16", "small", "ocean48"])
+@pytest.mark.parametrize("name", ["box16", "small", "ocean48", "ocean32"])
 @pytest.mark.parametrize("correction", [pm.STEP_LUMPED, pm.STEP_CONSISTENT])
 def test_project_step_matches_oracle(name, correction):
     b, op, ops = case(name)
@@ -318,7 +329,7 @@ def test_project_step_matches_oracle(name, correction):
     t2 = dev(op.column_field(b.theta[1]))
     # attainable tolerances: the thin ocean basin's pressure system floors near 1e-9 in FP64,
     # and its solution then carries kappa_eff * 1e-9 (about 1e-5) of rounding on either side
-    vtol, ptol, bar = (1e-11, 2e-9, 1e-5) if name == "ocean48" else (1e-12, 1e-12, 1e-8)
+    vtol, ptol, bar = (1e-11, 2e-9, 1e-5) if name.startswith("ocean") else (1e-12, 1e-12, 1e-8)
     vel = pm.Options(rtol=vtol, prec=pm.PREC_IC0, max_restarts=5)
     pres = pm.Options(rtol=ptol, prec=pm.PREC_LINE, max_restarts=5)
     ost = ostep.initial_state(ops.n)
