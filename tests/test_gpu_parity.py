@@ -22,7 +22,7 @@ def basin_cases():
         "box16": lambda: theta_basin(box_basin()),
         "small": lambda: small_basin(),
         "ocean48": lambda: ocean_basin(nx=48, ny=40, nz=9, dx=1e5),
-        "ocean32": lambda: ocean_basin(nx=40, ny=36, nz=32, dx=1e5),   # 32 levels: warp-task line kernel
+        "ocean32": lambda: ocean_basin(nx=40, ny=36, nz=32, dx=1e4),   # 32 levels, 10 km: warp-task line kernel
         "box2": lambda: box_basin(nh=2, nz=2),
     }
 
