@@ -682,8 +682,10 @@ __global__ void __launch_bounds__(LINE_FTPB) k_update_line(Geom g, const double*
   }
 }
 
-// The same fused iteration for 32-level columns, organised by warp instead of by block. A warp
-// task is TCOLS whole columns (TCOLS * 32 consecutive rows, since node id = column * 32 + k):
+// The same fused iteration for 32-level columns, organised by warp instead of by block. Every
+// warp owns an even, contiguous share of the columns (the grid is exactly the resident blocks, so
+// each SM gets the same work) and walks it in chunks of TCOLS whole columns (TCOLS * 32
+// consecutive rows, since node id = column * 32 + k):
 //   A (all lanes, coalesced): x += alpha p, r -= alpha w for level k = lane of each column, r
 //     staged into the warp's own shared-memory tile [column][level];
 //   B (lane = column): the Thomas sweep down and up the column in that tile;
@@ -694,11 +696,13 @@ __global__ void __launch_bounds__(LINE_FTPB) k_update_line(Geom g, const double*
 // upper bidiagonal, cp_k), a symmetric T has U = diag(w) L^T, so with t_k = r_k - lo_k y_{k-1},
 // y_k = t_k w_k and z = U^{-1} y,  (r, z) = y' diag(1/w) y = sum_k t_k y_k.
 constexpr int LINE_WNZ = 32;
+constexpr int LINE_WTPB = 256;   // 8 warps per block
+constexpr int LINE_WBLOCKS = 4;  // resident blocks per SM (64 registers per thread)
 template <int PROJ, int TCOLS>
-__global__ void __launch_bounds__(256, 3) k_update_line_w(Geom g, const double* __restrict__ F, double* __restrict__ x,
-                                                     double* __restrict__ r, const double* __restrict__ p,
-                                                     const double* __restrict__ w, double* __restrict__ z,
-                                                     const double* __restrict__ m, double* partials, PcgScalars* sc) {
+__global__ void __launch_bounds__(LINE_WTPB, LINE_WBLOCKS) k_update_line_w(
+    Geom g, const double* __restrict__ F, double* __restrict__ x, double* __restrict__ r,
+    const double* __restrict__ p, const double* __restrict__ w, double* __restrict__ z,
+    const double* __restrict__ m, double* partials, PcgScalars* sc) {
   constexpr int NZ = LINE_WNZ, LD = NZ + 1;
   extern __shared__ double smem[];
   if (sc_done(sc)) return;
@@ -708,12 +712,14 @@ __global__ void __launch_bounds__(256, 3) k_update_line_w(Geom g, const double* 
   double* ws = smem + wib * (TCOLS * LD);
   const int ncols = g.ncols;
   const int n = (int)g.n;
-  const int ntask = (ncols + TCOLS - 1) / TCOLS;
-  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  const int nwarps = gridDim.x * (LINE_WTPB / 32);
+  const int wg = blockIdx.x * (LINE_WTPB / 32) + wib;
+  // this warp's columns: [cbeg, cend), an even split of all columns over all warps
+  const int cbeg = (int)((int64_t)ncols * wg / nwarps);
+  const int cend = (int)((int64_t)ncols * (wg + 1) / nwarps);
   double v[4] = {0.0, 0.0, 0.0, 0.0};   // (r, r), (r, z), m'z, 1'r
-  for (int t = blockIdx.x * (blockDim.x >> 5) + wib; t < ntask; t += nwarps) {
-    const int c0 = t * TCOLS;
-    const int cc = min(TCOLS, ncols - c0);
+  for (int c0 = cbeg; c0 < cend; c0 += TCOLS) {
+    const int cc = min(TCOLS, cend - c0);
     const int row0 = c0 * NZ + lane;
 #pragma unroll 8
     for (int j = 0; j < cc; ++j) {
@@ -780,13 +786,12 @@ __global__ void __launch_bounds__(256, 3) k_update_line_w(Geom g, const double* 
 }
 
 #ifndef PM_LINE_WCOLS
-#define PM_LINE_WCOLS 32
+#define PM_LINE_WCOLS 16
 #endif
-constexpr int LINE_WCOLS = PM_LINE_WCOLS;   // columns per warp task
-constexpr int LINE_WTPB = 256;              // 8 warps per block
+constexpr int LINE_WCOLS = PM_LINE_WCOLS;   // columns per chunk of a warp's share
 
-// Launch of k_update_line_w: as many warps as make the tasks an equal count per warp, within the
-// kernel's residency and the partials buffer (4 lanes per block).
+// Launch of k_update_line_w: exactly the resident blocks (capped by the partials buffer, 4 lanes
+// per block, and by one column per warp).
 void update_line_w(pm_operator* op, int which, bool proj, double* x, cudaStream_t s) {
   SolveCtx* c = op->ctx;
   Geom g = geom_of(op);
@@ -799,12 +804,9 @@ void update_line_w(pm_operator* op, int which, bool proj, double* x, cudaStream_
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_line_w<1, LINE_WCOLS>, LINE_WTPB, smem);
     slots = std::max(1, per_sm) * op->num_sms;
   }
-  const int64_t ntask = (op->ncols + LINE_WCOLS - 1) / LINE_WCOLS;
-  const int64_t max_blocks = std::min<int64_t>(slots, (int64_t)NPART * MAX_GRID / 4);
-  const int64_t wpb = LINE_WTPB / 32;
-  const int64_t per_warp = std::max<int64_t>(1, (ntask + max_blocks * wpb - 1) / (max_blocks * wpb));
-  const int64_t warps = (ntask + per_warp - 1) / per_warp;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(max_blocks, (warps + wpb - 1) / wpb));
+  int64_t blocks = std::min<int64_t>(slots, (int64_t)NPART * MAX_GRID / 4);
+  blocks = std::min<int64_t>(blocks, (op->ncols + LINE_WTPB / 32 - 1) / (LINE_WTPB / 32));
+  const int grid = (int)std::max<int64_t>(1, blocks);
   const double* F = op->d_line[which];
   if (proj)
     k_update_line_w<1, LINE_WCOLS><<<grid, LINE_WTPB, smem, s>>>(g, F, x, c->r, c->p, c->w, c->z, op->d_m, c->partials, c->sc);
