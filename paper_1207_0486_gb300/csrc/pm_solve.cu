@@ -682,10 +682,10 @@ __global__ void __launch_bounds__(LINE_FTPB) k_update_line(Geom g, const double*
   }
 }
 
-// The same fused iteration for 32-level columns, organised by warp instead of by block. Every
-// warp owns an even, contiguous share of the columns (the grid is exactly the resident blocks, so
-// each SM gets the same work) and walks it in chunks of TCOLS whole columns (TCOLS * 32
-// consecutive rows, since node id = column * 32 + k):
+// The same fused iteration for 32-level columns, organised by warp instead of by block. A task is
+// TCOLS = 32 whole columns (TCOLS * 32 consecutive rows, since node id = column * 32 + k); every
+// warp owns an even, contiguous share of the tasks and the grid is exactly the resident blocks,
+// so each SM gets the same work. Per task:
 //   A (all lanes, coalesced): x += alpha p, r -= alpha w for level k = lane of each column, r
 //     staged into the warp's own shared-memory tile [column][level];
 //   B (lane = column): the Thomas sweep down and up the column in that tile;
@@ -697,7 +697,7 @@ __global__ void __launch_bounds__(LINE_FTPB) k_update_line(Geom g, const double*
 // y_k = t_k w_k and z = U^{-1} y,  (r, z) = y' diag(1/w) y = sum_k t_k y_k.
 constexpr int LINE_WNZ = 32;
 constexpr int LINE_WTPB = 256;   // 8 warps per block
-constexpr int LINE_WBLOCKS = 4;  // resident blocks per SM (64 registers per thread)
+constexpr int LINE_WBLOCKS = 3;  // resident blocks per SM (8.4 KB of shared memory per warp)
 template <int PROJ, int TCOLS>
 __global__ void __launch_bounds__(LINE_WTPB, LINE_WBLOCKS) k_update_line_w(
     Geom g, const double* __restrict__ F, double* __restrict__ x, double* __restrict__ r,
@@ -714,12 +714,15 @@ __global__ void __launch_bounds__(LINE_WTPB, LINE_WBLOCKS) k_update_line_w(
   const int n = (int)g.n;
   const int nwarps = gridDim.x * (LINE_WTPB / 32);
   const int wg = blockIdx.x * (LINE_WTPB / 32) + wib;
-  // this warp's columns: [cbeg, cend), an even split of all columns over all warps
-  const int cbeg = (int)((int64_t)ncols * wg / nwarps);
-  const int cend = (int)((int64_t)ncols * (wg + 1) / nwarps);
+  // this warp's tasks (TCOLS columns each, the last one ragged): an even split of all tasks over
+  // all warps, so every block, hence every SM, gets the same work and every lane sweeps a column
+  const int ntask = (ncols + TCOLS - 1) / TCOLS;
+  const int tbeg = (int)((int64_t)ntask * wg / nwarps);
+  const int tend = (int)((int64_t)ntask * (wg + 1) / nwarps);
   double v[4] = {0.0, 0.0, 0.0, 0.0};   // (r, r), (r, z), m'z, 1'r
-  for (int c0 = cbeg; c0 < cend; c0 += TCOLS) {
-    const int cc = min(TCOLS, cend - c0);
+  for (int t = tbeg; t < tend; ++t) {
+    const int c0 = t * TCOLS;
+    const int cc = min(TCOLS, ncols - c0);
     const int row0 = c0 * NZ + lane;
 #pragma unroll 8
     for (int j = 0; j < cc; ++j) {
@@ -785,13 +788,12 @@ __global__ void __launch_bounds__(LINE_WTPB, LINE_WBLOCKS) k_update_line_w(
   }
 }
 
-#ifndef PM_LINE_WCOLS
-#define PM_LINE_WCOLS 16
-#endif
-constexpr int LINE_WCOLS = PM_LINE_WCOLS;   // columns per chunk of a warp's share
+// Columns per task = lanes: every lane of a warp sweeps a column (an FP64 instruction costs the
+// FP64 pipe the same with idle lanes, and the sweep is a third of the kernel's FP64 work).
+constexpr int LINE_WCOLS = 32;
 
 // Launch of k_update_line_w: exactly the resident blocks (capped by the partials buffer, 4 lanes
-// per block, and by one column per warp).
+// per block, and by one task per warp).
 void update_line_w(pm_operator* op, int which, bool proj, double* x, cudaStream_t s) {
   SolveCtx* c = op->ctx;
   Geom g = geom_of(op);
@@ -805,7 +807,8 @@ void update_line_w(pm_operator* op, int which, bool proj, double* x, cudaStream_
     slots = std::max(1, per_sm) * op->num_sms;
   }
   int64_t blocks = std::min<int64_t>(slots, (int64_t)NPART * MAX_GRID / 4);
-  blocks = std::min<int64_t>(blocks, (op->ncols + LINE_WTPB / 32 - 1) / (LINE_WTPB / 32));
+  const int64_t ntask = (op->ncols + LINE_WCOLS - 1) / LINE_WCOLS;
+  blocks = std::min<int64_t>(blocks, (ntask + LINE_WTPB / 32 - 1) / (LINE_WTPB / 32));
   const int grid = (int)std::max<int64_t>(1, blocks);
   const double* F = op->d_line[which];
   if (proj)
