@@ -276,6 +276,11 @@ __global__ void __launch_bounds__(128) k_ic0_factor(Geom g, ColourMap cmap,
   }
 }
 
+__global__ void k_recip(double* __restrict__ d, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = 1.0 / d[i];
+}
+
 int grid_for(int64_t n, int threads, int sms) {
   int64_t gsz = (n + threads - 1) / threads;
   const int64_t cap = (int64_t)sms * 16;
@@ -389,6 +394,13 @@ int launch_ic0_factor(pm_operator* op, int which, double shift, int* breakdown, 
   if (st) return st;
   *breakdown = h_bd;
   f.shift = shift;
+  if (!h_bd) {
+    // The sweeps multiply by 1 / L_ii: an FP64 division costs the FP64 pipe about ten times an
+    // FMA, and each colour phase has only a few FMAs per row. The factor itself (computed with the
+    // divisions above) is unchanged; only its stored diagonal becomes the reciprocal.
+    k_recip<<<grid_for(op->n, 256, op->num_sms), 256, 0, s>>>(f.F + (int64_t)DIAG_SLOT * op->n, op->n);
+    count_launch();
+  }
   f.ok = h_bd == 0;
   return cuda_check(cudaGetLastError(), "k_ic0_factor");
 }

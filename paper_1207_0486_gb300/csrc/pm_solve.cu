@@ -431,6 +431,7 @@ struct CMap {
 
 // Forward (FWD = 1): y_i = (r_i - sum_{colour(j) < c} L_ij y_j) / L_ii over rows of colour c.
 // Backward (FWD = 0): z_i = (y_i - sum_{colour(j) > c} L_ji z_j) / L_ii, in place on y.
+// The factor's diagonal slot holds 1 / L_ii (a multiply instead of an FP64 division).
 template <int COLOUR, int FWD>
 __global__ void __launch_bounds__(TPB) k_ic0_sweep(Geom g, CMap cm, const int32_t* __restrict__ cls_cols,
                                                    int64_t cls_off, int64_t cls_cnt, const double* __restrict__ F,
@@ -462,7 +463,7 @@ __global__ void __launch_bounds__(TPB) k_ic0_sweep(Geom g, CMap cm, const int32_
       if (nb < 0) continue;
       acc = fma(-F[(int64_t)s * g.n + pi], y[(int64_t)nb * nz + kk], acc);
     }
-    y[row] = acc / F[(int64_t)DIAG_SLOT * g.n + pi];
+    y[row] = acc * F[(int64_t)DIAG_SLOT * g.n + pi];
   }
 }
 
@@ -1588,7 +1589,7 @@ __global__ void __launch_bounds__(TPB) k32_ic0_sweep(Geom g, CMap cm, const int3
       if (nb < 0) continue;
       acc = fmaf(-F[(int64_t)s * g.n + pi], y[(int64_t)nb * nz + kk], acc);
     }
-    y[row] = acc / F[(int64_t)DIAG_SLOT * g.n + pi];
+    y[row] = acc * F[(int64_t)DIAG_SLOT * g.n + pi];
   }
 }
 
