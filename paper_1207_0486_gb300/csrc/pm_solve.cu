@@ -1560,6 +1560,164 @@ __global__ void __launch_bounds__(LINE_UCOLS) k32_update_line(Geom g, const floa
   }
 }
 
+// FP32 version of k_update_line_w (32-level columns, warp tasks of 32 columns, no block
+// barriers); x stays FP64 and the dots are accumulated term by term in FP64. mode as
+// k32_update_line: 0 first step, 1 a full iteration, 2 finish an iteration after a residual
+// replacement. (r, z) = sum_k t_k y_k from the sweep (symmetric column blocks, see
+// k_update_line_w).
+template <int PROJ>
+__global__ void __launch_bounds__(LINE_WTPB, 4) k32_update_line_w(Geom g, const float* __restrict__ F,
+                                                              double* __restrict__ x, float* __restrict__ r,
+                                                              const float* __restrict__ p, const float* __restrict__ w,
+                                                              float* __restrict__ z, const double* __restrict__ m,
+                                                              double* partials, PcgScalars* sc, int mode) {
+  constexpr int NZ = LINE_WNZ, LD = NZ + 1, TC = LINE_WCOLS;
+  extern __shared__ float smf[];
+  const int update = mode == 1;
+  if (mode != 0 && sc_done(sc)) return;
+  const double alpha_d = update ? sc->alpha : 0.0;
+  const float alpha = (float)alpha_d;
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  float* ws = smf + wib * (TC * LD);
+  const int ncols = g.ncols;
+  const int n = (int)g.n;
+  const int nwarps = gridDim.x * (LINE_WTPB / 32);
+  const int wg = blockIdx.x * (LINE_WTPB / 32) + wib;
+  const int ntask = (ncols + TC - 1) / TC;
+  const int tbeg = (int)((int64_t)ntask * wg / nwarps);
+  const int tend = (int)((int64_t)ntask * (wg + 1) / nwarps);
+  double v[4] = {0.0, 0.0, 0.0, 0.0};   // (r, r), (r, z), m'z, 1'r
+  for (int t = tbeg; t < tend; ++t) {
+    const int c0 = t * TC;
+    const int cc = min(TC, ncols - c0);
+    const int row0 = c0 * NZ + lane;
+#pragma unroll 8
+    for (int j = 0; j < cc; ++j) {
+      const int row = row0 + j * NZ;
+      float ri = r[row];
+      if (update) {
+        x[row] = fma(alpha_d, (double)p[row], x[row]);
+        ri = fmaf(-alpha, w[row], ri);
+        r[row] = ri;
+      }
+      ws[j * LD + lane] = ri;
+      v[0] = fma((double)ri, (double)ri, v[0]);
+      if (PROJ) v[3] += (double)ri;
+    }
+    __syncwarp();
+    if (lane < cc) {
+      const int col = c0 + lane;
+      float* cs = ws + lane * LD;
+      float y = 0.f;
+      double rz = 0.0;
+#pragma unroll 8
+      for (int k = 0; k < NZ; ++k) {
+        const int li = k * ncols + col;
+        const float tk = fmaf(-F[li], y, cs[k]);
+        y = tk * F[n + li];
+        rz = fma((double)tk, (double)y, rz);
+        cs[k] = y;
+      }
+      float zn = y;
+#pragma unroll 8
+      for (int k = NZ - 2; k >= 0; --k) {
+        const int li = k * ncols + col;
+        zn = fmaf(-F[2 * n + li], zn, cs[k]);
+        cs[k] = zn;
+      }
+      v[1] += rz;
+    }
+    __syncwarp();
+#pragma unroll 8
+    for (int j = 0; j < cc; ++j) {
+      const int row = row0 + j * NZ;
+      const float zi = ws[j * LD + lane];
+      z[row] = zi;
+      if (PROJ) v[2] = fma(m[row], (double)zi, v[2]);
+    }
+    __syncwarp();
+  }
+  if (grid_sum<4>(v, partials, &sc->count[4]) && threadIdx.x == 0) {
+    const double c = PROJ ? v[2] / sc->one_m : 0.0;
+    const double rho_new = v[1] - c * v[3];
+    if (mode == 0) {
+      sc->proj_c = c;
+      sc->rho = rho_new;
+      sc->beta = 0.0;
+      if ((!(rho_new > 0.0) || !isfinite(rho_new)) && !sc->done) {
+        sc->status = PM_BREAKDOWN;
+        sc->done = 1;
+      }
+    } else if (mode == 2) {
+      sc->proj_c = c;
+      sc->beta = rho_new / sc->rho;
+      sc->rho = rho_new;
+      if (!(rho_new > 0.0) || !isfinite(rho_new)) {
+        sc->status = PM_BREAKDOWN;
+        sc->done = 1;
+      }
+    } else {
+      sc->iter += 1;
+      sc->rr = v[0];
+      if (v[0] <= sc->tol2) {
+        sc->done = 1;
+      } else if (sc->iter >= sc->max_iter) {
+        sc->status = PM_NOT_CONVERGED;
+        sc->done = 1;
+      } else if (v[0] <= sc->aux[2]) {
+        sc->done = 2;
+      } else {
+        sc->proj_c = c;
+        sc->beta = rho_new / sc->rho;
+        sc->rho = rho_new;
+        if (!(rho_new > 0.0) || !isfinite(rho_new)) {
+          sc->status = PM_BREAKDOWN;
+          sc->done = 1;
+        }
+      }
+    }
+  }
+}
+
+// The FP32 fused update + line solve (mode as k32_update_line): warp tasks for 32-level columns,
+// the block kernel otherwise. One launch; the caller counts it.
+void update_line32(pm_operator* op, int which, bool proj, double* x, int mode, cudaStream_t s) {
+  SolveCtx* c = op->ctx;
+  Geom g = geom_of(op);
+  if (op->nz == LINE_WNZ) {
+    const size_t smem = (size_t)(LINE_WTPB / 32) * LINE_WCOLS * (LINE_WNZ + 1) * sizeof(float);
+    static int slots = 0;
+    if (!slots) {
+      cudaFuncSetAttribute(k32_update_line_w<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(k32_update_line_w<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      int per_sm = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k32_update_line_w<1>, LINE_WTPB, smem);
+      slots = std::max(1, per_sm) * op->num_sms;
+    }
+    int64_t blocks = std::min<int64_t>(slots, (int64_t)NPART * MAX_GRID / 4);
+    const int64_t ntask = (op->ncols + LINE_WCOLS - 1) / LINE_WCOLS;
+    blocks = std::min<int64_t>(blocks, (ntask + LINE_WTPB / 32 - 1) / (LINE_WTPB / 32));
+    const int grid = (int)std::max<int64_t>(1, blocks);
+    if (proj)
+      k32_update_line_w<1><<<grid, LINE_WTPB, smem, s>>>(g, op->d_line32[which], x, c->r32, c->p32, c->w32, c->z32,
+                                                          op->d_m, c->partials, c->sc_in, mode);
+    else
+      k32_update_line_w<0><<<grid, LINE_WTPB, smem, s>>>(g, op->d_line32[which], x, c->r32, c->p32, c->w32, c->z32,
+                                                          op->d_m, c->partials, c->sc_in, mode);
+    return;
+  }
+  const int64_t ntiles = (op->ncols + LINE_UCOLS - 1) / LINE_UCOLS;
+  int grid = (int)std::min<int64_t>(ntiles, std::min<int64_t>((int64_t)op->num_sms * 8, MAX_GRID));
+  const size_t smem = (size_t)LINE_UCOLS * (op->nz + 1) * sizeof(float);
+  if (proj)
+    k32_update_line<1><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], x, c->r32, c->p32, c->w32, c->z32,
+                                                      op->d_m, c->partials, c->sc_in, mode);
+  else
+    k32_update_line<0><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], x, c->r32, c->p32, c->w32, c->z32,
+                                                      op->d_m, c->partials, c->sc_in, mode);
+}
+
 // FP32 IC0 colour sweep (as k_ic0_sweep).
 template <int COLOUR, int FWD>
 __global__ void __launch_bounds__(TPB) k32_ic0_sweep(Geom g, CMap cm, const int32_t* __restrict__ cls_cols,
@@ -1700,17 +1858,9 @@ void inner_iter(pm_operator* op, int which, const TV* val32, bool proj, int prec
     k32_spmv<MASKC, TV><<<G, TPB, 0, s>>>(g, val32, c->p32, c->w32, c->partials, c->sc_in);
   }
   if (prec == PM_PREC_LINE) {
-    const int64_t ntiles = (op->ncols + LINE_UCOLS - 1) / LINE_UCOLS;
-    int grid = (int)std::min<int64_t>(ntiles, std::min<int64_t>((int64_t)op->num_sms * 8, MAX_GRID));
-    const size_t smem = (size_t)LINE_UCOLS * (op->nz + 1) * sizeof(float);
     {
       KtScope t(PM_KT_LINE, 1, s);
-      if (proj)
-        k32_update_line<1><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], x, c->r32, c->p32, c->w32,
-                                                          c->z32, op->d_m, c->partials, c->sc_in, 1);
-      else
-        k32_update_line<0><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], x, c->r32, c->p32, c->w32,
-                                                          c->z32, op->d_m, c->partials, c->sc_in, 1);
+      update_line32(op, which, proj, x, 1, s);
     }
     {
       KtScope t(PM_KT_PUPDATE, 1, s);
@@ -1756,15 +1906,7 @@ void inner_first(pm_operator* op, int which, bool proj, int prec, const float* d
   const int G = grid_for(op->n, TPB, op->num_sms);
   if (!reset_p) {
     if (prec == PM_PREC_LINE) {
-      const int64_t ntiles = (op->ncols + LINE_UCOLS - 1) / LINE_UCOLS;
-      int grid = (int)std::min<int64_t>(ntiles, std::min<int64_t>((int64_t)op->num_sms * 8, MAX_GRID));
-      const size_t smem = (size_t)LINE_UCOLS * (op->nz + 1) * sizeof(float);
-      if (proj)
-        k32_update_line<1><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], x, c->r32, c->p32, c->w32, c->z32,
-                                                          op->d_m, c->partials, c->sc_in, 2);
-      else
-        k32_update_line<0><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], x, c->r32, c->p32, c->w32, c->z32,
-                                                          op->d_m, c->partials, c->sc_in, 2);
+      update_line32(op, which, proj, x, 2, s);
       k32_pupd<1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, c->p32, c->sc_in, 0);
     } else if (prec == PM_PREC_IC0) {
       ic0_apply32(op, which, c->r32, c->z32, c->sc_in, 0, s);
@@ -1780,15 +1922,7 @@ void inner_first(pm_operator* op, int which, bool proj, int prec, const float* d
     return;
   }
   if (prec == PM_PREC_LINE) {
-    const int64_t ntiles = (op->ncols + LINE_UCOLS - 1) / LINE_UCOLS;
-    int grid = (int)std::min<int64_t>(ntiles, std::min<int64_t>((int64_t)op->num_sms * 8, MAX_GRID));
-    const size_t smem = (size_t)LINE_UCOLS * (op->nz + 1) * sizeof(float);
-    if (proj)
-      k32_update_line<1><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], x, c->r32, c->p32, c->w32,
-                                                        c->z32, op->d_m, c->partials, c->sc_in, 0);
-    else
-      k32_update_line<0><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], x, c->r32, c->p32, c->w32,
-                                                        c->z32, op->d_m, c->partials, c->sc_in, 0);
+    update_line32(op, which, proj, x, 0, s);
     k32_pupd<1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, c->p32, c->sc_in, 1);
   } else if (prec == PM_PREC_IC0) {
     ic0_apply32(op, which, c->r32, c->z32, c->sc_in, 0, s);

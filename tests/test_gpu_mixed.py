@@ -27,7 +27,8 @@ _cache = {}
 def case(name):
     if name not in _cache:
         b = {"box16": lambda: theta_basin(box_basin()), "small": small_basin,
-             "ocean48": lambda: ocean_basin(nx=48, ny=40, nz=9, dx=1e5)}[name]()
+             "ocean48": lambda: ocean_basin(nx=48, ny=40, nz=9, dx=1e5),
+             "ocean32": lambda: ocean_basin(nx=40, ny=36, nz=32, dx=1e4)}[name]()
         _cache[name] = (b, pm.assemble_operator(b), fem.assemble(b))
     return _cache[name]
 
@@ -77,7 +78,7 @@ def test_mixed_solve_matches_fp64_oracle(name, which, precision, prec):
     assert st.rel_residual_true <= max(rtol, st.rel_residual_floor)
     A = oracle_matrix(ops, which)
     if which == pm.OP_PRESSURE:
-        ref = opcg.pressure_solve(A, ops.m, rhs, rtol=1e-12 if name != "ocean48" else 2e-9)
+        ref = opcg.pressure_solve(A, ops.m, rhs, rtol=1e-12 if not name.startswith("ocean") else 2e-9)
     else:
         ref = opcg.pcg(A, rhs, rtol=1e-13, precond=opcg.jacobi_preconditioner(A))
     xg = x.cpu().numpy()
@@ -85,6 +86,13 @@ def test_mixed_solve_matches_fp64_oracle(name, which, precision, prec):
     kappa = lanczos_kappa(A, rhs, ops.m if which == pm.OP_PRESSURE else None)
     bound = 4 * kappa * (max(st.rel_residual_true, st.rel_residual_floor) + ref.rel_res_true)
     assert err <= max(bound, 1e-12), (err, kappa, bound)
+
+
+@pytest.mark.parametrize("which", [pm.OP_VEL_U1, pm.OP_PRESSURE])
+@pytest.mark.parametrize("precision", [pm.FP32_REFINE, pm.BF16_REFINE])
+def test_mixed_line_solve_on_32_level_columns(which, precision):
+    """32-level columns take the warp-task FP32 line kernel."""
+    test_mixed_solve_matches_fp64_oracle("ocean32", which, precision, pm.PREC_LINE)
 
 
 @pytest.mark.parametrize("precision", [pm.FP32_REFINE, pm.BF16_REFINE])
