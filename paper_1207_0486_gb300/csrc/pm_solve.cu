@@ -1339,9 +1339,10 @@ __global__ void __launch_bounds__(TPB, 4) k32_spmv(Geom g, const TV* __restrict_
   }
 }
 
-// x += alpha p (x in FP64), r -= alpha w (FP32); INLINE_Z: z = dinv r (Jacobi) and its reductions.
+// d += alpha p, r -= alpha w (FP32; d is the correction since the last residual replacement,
+// folded into the FP64 x there); INLINE_Z: z = dinv r (Jacobi) and its reductions.
 template <int PROJ, int INLINE_Z>
-__global__ void __launch_bounds__(TPB) k32_update(int64_t n, double* __restrict__ x, float* __restrict__ r,
+__global__ void __launch_bounds__(TPB) k32_update(int64_t n, float* __restrict__ d, float* __restrict__ r,
                                                   const float* __restrict__ p, const float* __restrict__ w,
                                                   const float* __restrict__ dinv, const double* __restrict__ m,
                                                   double* partials, PcgScalars* sc) {
@@ -1350,7 +1351,7 @@ __global__ void __launch_bounds__(TPB) k32_update(int64_t n, double* __restrict_
   const float alpha = (float)alpha_d;
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] = fma(alpha_d, (double)p[i], x[i]);
+    d[i] = fmaf(alpha, p[i], d[i]);
     const float ri = fmaf(-alpha, w[i], r[i]);
     r[i] = ri;
     v[0] = fma((double)ri, (double)ri, v[0]);
@@ -1433,6 +1434,14 @@ __global__ void __launch_bounds__(TPB) k32_pupd(int64_t n, const float* __restri
   }
 }
 
+// x += d (FP64), d = 0: the inner solve's FP32 correction folded into the FP64 iterate.
+__global__ void k32_fold(int64_t n, double* __restrict__ x, float* __restrict__ d) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += (double)d[i];
+    d[i] = 0.f;
+  }
+}
+
 __global__ void k32_from64(int64_t n, const double* __restrict__ r64, float* __restrict__ r32) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     r32[i] = (float)r64[i];
@@ -1453,11 +1462,11 @@ __global__ void k_cvt(int64_t n, const double* __restrict__ in, T* __restrict__ 
 // FP32 vertical-line solve fused with the inner update (as k_update_line).
 template <int PROJ>
 __global__ void __launch_bounds__(LINE_UCOLS) k32_update_line(Geom g, const float* __restrict__ F,
-                                                            double* __restrict__ x, float* __restrict__ r,
+                                                            float* __restrict__ d, float* __restrict__ r,
                                                             const float* __restrict__ p, const float* __restrict__ w,
                                                             float* __restrict__ z, const double* __restrict__ m,
                                                             double* partials, PcgScalars* sc, int mode) {
-  // mode 0: first step (z, rho, beta = 0); 1: a full iteration (x, r update, z, rho, beta);
+  // mode 0: first step (z, rho, beta = 0); 1: a full iteration (d, r update, z, rho, beta);
   // 2: finish an iteration after a residual replacement (z, rho_new, beta = rho_new / rho)
   extern __shared__ float smf[];
   const int update = mode == 1;
@@ -1478,7 +1487,7 @@ __global__ void __launch_bounds__(LINE_UCOLS) k32_update_line(Geom g, const floa
       const int row = row0 + i;
       float ri = r[row];
       if (update) {
-        x[row] = fma(alpha_d, (double)p[row], x[row]);
+        d[row] = fmaf(alpha, p[row], d[row]);
         ri = fmaf(-alpha, w[row], ri);
         r[row] = ri;
       }
@@ -1561,13 +1570,14 @@ __global__ void __launch_bounds__(LINE_UCOLS) k32_update_line(Geom g, const floa
 }
 
 // FP32 version of k_update_line_w (32-level columns, warp tasks of 32 columns, no block
-// barriers); x stays FP64 and the dots are accumulated term by term in FP64. mode as
+// barriers); the FP32 correction d takes alpha p (folded into the FP64 x at each residual
+// replacement) and the dots are accumulated term by term in FP64. mode as
 // k32_update_line: 0 first step, 1 a full iteration, 2 finish an iteration after a residual
 // replacement. (r, z) = sum_k t_k y_k from the sweep (symmetric column blocks, see
 // k_update_line_w).
 template <int PROJ>
 __global__ void __launch_bounds__(LINE_WTPB, 4) k32_update_line_w(Geom g, const float* __restrict__ F,
-                                                              double* __restrict__ x, float* __restrict__ r,
+                                                              float* __restrict__ d, float* __restrict__ r,
                                                               const float* __restrict__ p, const float* __restrict__ w,
                                                               float* __restrict__ z, const double* __restrict__ m,
                                                               double* partials, PcgScalars* sc, int mode) {
@@ -1597,7 +1607,7 @@ __global__ void __launch_bounds__(LINE_WTPB, 4) k32_update_line_w(Geom g, const 
       const int row = row0 + j * NZ;
       float ri = r[row];
       if (update) {
-        x[row] = fma(alpha_d, (double)p[row], x[row]);
+        d[row] = fmaf(alpha, p[row], d[row]);
         ri = fmaf(-alpha, w[row], ri);
         r[row] = ri;
       }
@@ -1700,10 +1710,10 @@ void update_line32(pm_operator* op, int which, bool proj, double* x, int mode, c
     blocks = std::min<int64_t>(blocks, (ntask + LINE_WTPB / 32 - 1) / (LINE_WTPB / 32));
     const int grid = (int)std::max<int64_t>(1, blocks);
     if (proj)
-      k32_update_line_w<1><<<grid, LINE_WTPB, smem, s>>>(g, op->d_line32[which], x, c->r32, c->p32, c->w32, c->z32,
+      k32_update_line_w<1><<<grid, LINE_WTPB, smem, s>>>(g, op->d_line32[which], c->d32, c->r32, c->p32, c->w32, c->z32,
                                                           op->d_m, c->partials, c->sc_in, mode);
     else
-      k32_update_line_w<0><<<grid, LINE_WTPB, smem, s>>>(g, op->d_line32[which], x, c->r32, c->p32, c->w32, c->z32,
+      k32_update_line_w<0><<<grid, LINE_WTPB, smem, s>>>(g, op->d_line32[which], c->d32, c->r32, c->p32, c->w32, c->z32,
                                                           op->d_m, c->partials, c->sc_in, mode);
     return;
   }
@@ -1711,10 +1721,10 @@ void update_line32(pm_operator* op, int which, bool proj, double* x, int mode, c
   int grid = (int)std::min<int64_t>(ntiles, std::min<int64_t>((int64_t)op->num_sms * 8, MAX_GRID));
   const size_t smem = (size_t)LINE_UCOLS * (op->nz + 1) * sizeof(float);
   if (proj)
-    k32_update_line<1><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], x, c->r32, c->p32, c->w32, c->z32,
+    k32_update_line<1><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], c->d32, c->r32, c->p32, c->w32, c->z32,
                                                       op->d_m, c->partials, c->sc_in, mode);
   else
-    k32_update_line<0><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], x, c->r32, c->p32, c->w32, c->z32,
+    k32_update_line<0><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], c->d32, c->r32, c->p32, c->w32, c->z32,
                                                       op->d_m, c->partials, c->sc_in, mode);
 }
 
@@ -1837,13 +1847,15 @@ int read_inner(SolveCtx* c, cudaStream_t s) {
   return st;
 }
 
-// Algorithmic bytes per inner iteration per row (values at vbytes each).
-double bytes_per_inner(const pm_operator* op, int prec, int vbytes) {
+// Algorithmic bytes per inner iteration per row (values at vbytes each; vectors FP32, the
+// correction d read and written in FP32).
+double bytes_per_inner(const pm_operator* op, int prec, int vbytes, bool proj) {
   const double n = (double)op->n;
   double b = n * (15 * vbytes + 4 + 4);                       // SpMV: values, p, w
-  if (prec == PM_PREC_LINE) b += n * (16 + 8 + 12 + 4 + 4 + 12);  // fused update + line, p-update
-  else if (prec == PM_PREC_IC0) b += n * (24 + 2 * 8 * 4 + 4 * 4 + 8 + 12);
-  else b += n * (20 + 8 + 16);                                 // Jacobi update, p-update
+  if (prec == PM_PREC_LINE) b += n * (8 + 8 + 4 + 4 + 12 + 4 + 12);  // d, r r/w; p, w; factors; z; p-update
+  else if (prec == PM_PREC_IC0) b += n * (8 + 8 + 4 + 4 + 2 * 8 * 4 + 4 * 4 + 8 + 12);
+  else b += n * (8 + 8 + 4 + 4 + 4 + 4 * 4);                   // Jacobi update (z inline), p-update
+  if (proj) b += n * 8;                                         // m'z
   return b;
 }
 
@@ -1870,7 +1882,7 @@ void inner_iter(pm_operator* op, int which, const TV* val32, bool proj, int prec
   } else if (prec == PM_PREC_IC0) {
     {
       KtScope t(PM_KT_UPDATE, 1, s);
-      k32_update<0, 0><<<G, TPB, 0, s>>>(op->n, x, c->r32, c->p32, c->w32, dinv32, op->d_m, c->partials, c->sc_in);
+      k32_update<0, 0><<<G, TPB, 0, s>>>(op->n, c->d32, c->r32, c->p32, c->w32, dinv32, op->d_m, c->partials, c->sc_in);
     }
     {
       KtScope t(PM_KT_IC0, 16, s);
@@ -1886,8 +1898,8 @@ void inner_iter(pm_operator* op, int which, const TV* val32, bool proj, int prec
   } else {
     {
       KtScope t(PM_KT_UPDATE, 1, s);
-      if (proj) k32_update<1, 1><<<G, TPB, 0, s>>>(op->n, x, c->r32, c->p32, c->w32, dinv32, op->d_m, c->partials, c->sc_in);
-      else k32_update<0, 1><<<G, TPB, 0, s>>>(op->n, x, c->r32, c->p32, c->w32, dinv32, op->d_m, c->partials, c->sc_in);
+      if (proj) k32_update<1, 1><<<G, TPB, 0, s>>>(op->n, c->d32, c->r32, c->p32, c->w32, dinv32, op->d_m, c->partials, c->sc_in);
+      else k32_update<0, 1><<<G, TPB, 0, s>>>(op->n, c->d32, c->r32, c->p32, c->w32, dinv32, op->d_m, c->partials, c->sc_in);
     }
     {
       KtScope t(PM_KT_PUPDATE, 1, s);
@@ -2013,6 +2025,7 @@ int mixed_run(pm_operator* op, int which, const double* b, double* x, const pm_s
     if ((st = cuda_check(cudaMemcpyAsync(c->sc_in, &in, sizeof(in), cudaMemcpyHostToDevice, s), "scalars"))) return st;
     k32_from64<<<G, TPB, 0, s>>>(op->n, c->r, c->r32);
     count_launch();
+    if ((st = cuda_check(cudaMemsetAsync(c->d32, 0, (size_t)op->n * sizeof(float), s), "d32"))) return st;
     inner_first(op, which, proj, prec, dinv32, x, true, s);
     if ((st = read_inner(c, s))) return st;
     int64_t issued = 0;
@@ -2028,11 +2041,13 @@ int mixed_run(pm_operator* op, int which, const double* b, double* x, const pm_s
         if ((st = read_inner(c, s))) return st;
         if (chunk < 64) chunk *= 2;
       }
-      // FP64 true residual into c->r
+      // fold the FP32 correction into x, then the FP64 true residual into c->r
+      k32_fold<<<G, TPB, 0, s>>>(op->n, x, c->d32);
+      count_launch();
       launch_residual<MASKC>(op, val64, bw, x, o->rtol, 1, s);
       if ((st = read_scalars(c, s))) return st;
       ++outer;
-      bytes += (double)op->n * (15 * 8 + 3 * 8);
+      bytes += (double)op->n * (15 * 8 + 3 * 8 + 16 + 8);   // FP64 residual; the fold of d into x
       rel_true = std::sqrt(c->sc_host->aux[0] / bb);
       rel_floor = std::ldexp(1.0, -53) * std::sqrt(c->sc_host->aux[1] / bb);
       // the refinement step did not halve the (compensated) true residual
@@ -2069,7 +2084,7 @@ int mixed_run(pm_operator* op, int which, const double* b, double* x, const pm_s
       if ((st = read_inner(c, s))) return st;
     }
     inner_total = c->sc_in_host->iter;
-    bytes += inner_total * bytes_per_inner(op, prec, vbytes);
+    bytes += inner_total * bytes_per_inner(op, prec, vbytes, proj);
   }
   if (proj) {
     k_cg_press_sums<<<G, TPB, 0, s>>>(op->n, b, x, op->d_m, 1, c->partials, c->sc);
