@@ -532,7 +532,7 @@ def run_ours(args):
     e2e = None
     time_loop = None
     fp64_fields_at = {}
-    k_m = max(2, min(args.steps, 3))
+    k_m = max(1, min(args.steps, 3))
     if not args.no_e2e:
         st.restore(snap)
         th_h = [torch.from_numpy(op.column_field(basin.theta[c])).pin_memory() for c in range(2)]
