@@ -65,6 +65,7 @@ static void free_operator(pm_operator* op) {
   cudaFree(op->d_coriolis);
   cudaFree(op->d_cls_cols);
   cudaFree(op->d_struct);
+  for (int c = 0; c < 3; ++c) cudaFree(op->d_keep[c]);
   cudaFree(op->d_m);
   for (int v = 0; v < VS_COUNT; ++v) {
     cudaFree(op->d_val[v]);
@@ -134,7 +135,7 @@ int64_t pm_operator_bytes(const pm_mesh_desc* d) {
   b += 3 * (int64_t)NSLOT * np * 4;            // FP32 copies of the solved operators (mixed precision)
   b += 3 * (int64_t)NSLOT * n * 8;             // IC0 factors of the three BDF2 velocity systems
   b += 4 * n * 12;                             // Jacobi diagonals
-  b += n * (8 + 2) + ncols * (7 * 4 + 8 + 8 + 2 + 16);
+  b += n * (8 + 2 + 3 * 2) + ncols * (7 * 4 + 8 + 8 + 2 + 16);   // m, structure, keep masks; columns
   b += 5 * n * 8 + (int64_t)NPART * MAX_GRID * 8;   // PCG workspace
   return b;
 }

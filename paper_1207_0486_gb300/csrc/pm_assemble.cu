@@ -276,6 +276,38 @@ __global__ void __launch_bounds__(128) k_ic0_factor(Geom g, ColourMap cmap,
   }
 }
 
+// Per velocity component c, per row: bit s set when slot s's neighbour exists and is not in c's
+// Dirichlet set (the columns the symmetric elimination keeps), bit 15 set when the row itself is
+// a Dirichlet row (an identity row of the eliminated operator).
+__global__ void k_keep_masks(Geom g, uint16_t* __restrict__ k0, uint16_t* __restrict__ k1, uint16_t* __restrict__ k2) {
+  const int nz = g.nz;
+  for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < g.n;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    const int col = (int)(row / nz);
+    const int k = (int)(row - (int64_t)col * nz);
+    int nb[NNBR];
+    uint8_t fl[NNBR];
+#pragma unroll
+    for (int q = 0; q < NNBR; ++q) {
+      nb[q] = q == 0 ? col : g.nbr[(int64_t)col * NNBR + q];
+      fl[q] = nb[q] >= 0 ? g.colflag[nb[q]] : 0;
+    }
+    uint16_t* outs[3] = {k0, k1, k2};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      uint32_t m = is_dirichlet(fl[0], k, nz, c) ? 0x8000u : 0u;
+#pragma unroll
+      for (int s = 0; s < NSLOT; ++s) {
+        const int q = slot_q(s);
+        const int kk = k + slot_dk(s);
+        const bool ok = nb[q] >= 0 && kk >= 0 && kk < nz && !is_dirichlet(fl[q], kk, nz, c);
+        m |= (ok ? 1u : 0u) << s;
+      }
+      outs[c][row] = (uint16_t)m;
+    }
+  }
+}
+
 __global__ void k_recip(double* __restrict__ d, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     d[i] = 1.0 / d[i];
@@ -327,7 +359,21 @@ int launch_assemble(pm_operator* op, cudaStream_t s) {
   st = cuda_check(cudaStreamSynchronize(s), "assemble");
   cudaFreeAsync(d_sum, s);
   if (st) return st;
+  if ((st = launch_keep_masks(op, s))) return st;
   return cuda_check(cudaGetLastError(), "assemble kernels");
+}
+
+int launch_keep_masks(pm_operator* op, cudaStream_t s) {
+  for (int c = 0; c < 3; ++c) {
+    if (op->d_keep[c]) continue;
+    int st = cuda_check(cudaMalloc((void**)&op->d_keep[c], (size_t)op->n * sizeof(uint16_t)), "cudaMalloc keep mask");
+    if (st) return st;
+    op->device_bytes += op->n * 2;
+  }
+  Geom g = geom_of(op);
+  k_keep_masks<<<grid_for(op->n, 256, op->num_sms), 256, 0, s>>>(g, op->d_keep[0], op->d_keep[1], op->d_keep[2]);
+  count_launch();
+  return cuda_check(cudaGetLastError(), "k_keep_masks");
 }
 
 int launch_dinv(pm_operator* op, int which, cudaStream_t s) {

@@ -213,6 +213,8 @@ struct pm_operator {
   double* d_coriolis = nullptr;
   int32_t* d_cls_cols = nullptr;    // columns grouped by parity class, [ncols]
   uint16_t* d_struct = nullptr;     // structural slot bits per row
+  uint16_t* d_keep[3] = {};         // per velocity component: bit s = slot s kept (neighbour present and
+                                    // not in the component's Dirichlet set), bit 15 = Dirichlet row
   double* d_val[pm::VS_COUNT] = {};
   float* d_val32[pm::VS_COUNT] = {};
   uint16_t* d_val16[pm::VS_COUNT] = {};  // bf16 bit patterns
@@ -269,6 +271,7 @@ int build_host_mesh(const pm_mesh_desc* d, const double* coriolis, HostMesh* out
 int launch_assemble(pm_operator* op, cudaStream_t s);
 int launch_ic0_factor(pm_operator* op, int which, double shift, int* breakdown, cudaStream_t s);
 int launch_dinv(pm_operator* op, int which, cudaStream_t s);
+int launch_keep_masks(pm_operator* op, cudaStream_t s);
 
 // pm_solve.cu
 int spmv(pm_operator* op, int which, const double* x, double* y, cudaStream_t s);

@@ -213,6 +213,33 @@ __device__ __forceinline__ double row_dot(const Geom& g, const TV* __restrict__ 
   return sum;
 }
 
+// Row r of component c's eliminated velocity operator times x, with the kept slots of the row
+// read from its precomputed mask (bit s: slot s's neighbour present and not Dirichlet; bit 15:
+// identity row). Same result as row_dot<c>, without the dependent column-flag loads.
+template <typename TV, typename TX>
+__device__ __forceinline__ double row_dot_keep(const Geom& g, const TV* __restrict__ val, const TX* __restrict__ x,
+                                               const uint16_t* __restrict__ keep, int row, int col, int k) {
+  const int nz = g.nz;
+  const int npad = (int)g.npad;
+  const uint32_t km = __ldg(keep + row);
+  if (km & 0x8000u) return (double)x[row];
+  int nb[NNBR];
+  nb[0] = col;
+#pragma unroll
+  for (int q = 1; q < NNBR; ++q) nb[q] = __ldg(g.nbr + col * NNBR + q);
+  TV a[NSLOT];
+#pragma unroll
+  for (int s = 0; s < NSLOT; ++s) a[s] = __ldg(val + s * npad + row);
+  double sum = 0.0;
+#pragma unroll
+  for (int s = 0; s < NSLOT; ++s) {
+    const bool ok = (km >> s) & 1u;
+    const double xv = (double)x[ok ? nb[slot_q(s)] * nz + k + slot_dk(s) : row];
+    sum = fma(ok ? (double)a[s] : 0.0, xv, sum);
+  }
+  return sum;
+}
+
 template <int MASKC>
 __global__ void __launch_bounds__(TPB) k_spmv(Geom g, const double* __restrict__ val,
                                               const double* __restrict__ x, double* __restrict__ y) {
@@ -352,7 +379,8 @@ __global__ void __launch_bounds__(TPB) k_cg_pupd(int64_t n, const double* __rest
 // 256 threads, at most 64 registers: 4 blocks (32 warps) per SM to hide the gather latency.
 template <int MASKC>
 __global__ void __launch_bounds__(TPB, 4) k_cg_spmv(Geom g, const double* __restrict__ val, const double* __restrict__ p,
-                                                    double* __restrict__ w, double* partials, PcgScalars* sc) {
+                                                    double* __restrict__ w, const uint16_t* __restrict__ keep,
+                                                    double* partials, PcgScalars* sc) {
   if (sc_done(sc)) return;
   double v[1] = {0.0};
   const int n = (int)g.n;
@@ -360,7 +388,7 @@ __global__ void __launch_bounds__(TPB, 4) k_cg_spmv(Geom g, const double* __rest
     const int col = row / g.nz;
     const int k = row - col * g.nz;
     bool d = false;
-    const double wi = row_dot<MASKC>(g, val, p, row, col, k, d);
+    const double wi = MASKC >= 0 ? row_dot_keep(g, val, p, keep, row, col, k) : row_dot<MASKC>(g, val, p, row, col, k, d);
     w[row] = wi;
     v[0] = fma(p[row], wi, v[0]);
   }
@@ -984,7 +1012,8 @@ void launch_iter(pm_operator* op, int which, const double* val, double* x, bool 
   const bool ic0 = prec == PM_PREC_IC0;
   {
     KtScope t(PM_KT_SPMV, 1, s);
-    k_cg_spmv<MASKC><<<G, TPB, 0, s>>>(g, val, c->p, c->w, c->partials, c->sc);
+    k_cg_spmv<MASKC><<<G, TPB, 0, s>>>(g, val, c->p, c->w, MASKC >= 0 ? op->d_keep[MASKC < 0 ? 0 : MASKC] : nullptr,
+                                       c->partials, c->sc);
   }
   if (prec == PM_PREC_LINE) {
     {
