@@ -1321,6 +1321,40 @@ __device__ __forceinline__ float row_dot32(const Geom& g, const TV* __restrict__
   return fmaf(a[DIAG_SLOT] - drop, xi, sum);
 }
 
+// row_dot32 for a velocity component through its keep mask (see row_dot_keep): a slot whose
+// neighbour is present but eliminated adds its value to the drop term.
+template <typename TV>
+__device__ __forceinline__ float row_dot32_keep(const Geom& g, const TV* __restrict__ val, const float* __restrict__ x,
+                                                const uint16_t* __restrict__ keep, int row, int col, int k) {
+  const int nz = g.nz;
+  const int npad = (int)g.npad;
+  const uint32_t km = __ldg(keep + row);
+  if (km & 0x8000u) return x[row];
+  int nb[NNBR];
+  nb[0] = col;
+#pragma unroll
+  for (int q = 1; q < NNBR; ++q) nb[q] = __ldg(g.nbr + col * NNBR + q);
+  float a[NSLOT];
+#pragma unroll
+  for (int s = 0; s < NSLOT; ++s) a[s] = ldv(val, s * npad + row);
+  const float xi = x[row];
+  float sum = 0.f, drop = 0.f;
+#pragma unroll
+  for (int s = 0; s < NSLOT; ++s) {
+    if (s == DIAG_SLOT) continue;
+    const int q = slot_q(s);
+    const int kk = k + slot_dk(s);
+    bool exists = nb[q] >= 0;
+    if (slot_dk(s) < 0) exists = exists && kk >= 0;
+    if (slot_dk(s) > 0) exists = exists && kk < nz;
+    const bool keep_s = (km >> s) & 1u;
+    drop += (exists && !keep_s) ? a[s] : 0.f;
+    const float xv = x[keep_s ? nb[q] * nz + kk : row];
+    sum = fmaf(keep_s ? a[s] : 0.f, xv - xi, sum);
+  }
+  return fmaf(a[DIAG_SLOT] - drop, xi, sum);
+}
+
 // Low-precision copy in difference form: off-diagonals rounded, diagonal slot = FP64 row sum
 // (zero_rowsum: exactly 0, the pure-Neumann operator).
 template <typename T>
@@ -1345,14 +1379,15 @@ __global__ void k_cvt_diff(int64_t n, int64_t npad, const double* __restrict__ v
 
 template <int MASKC, typename TV>
 __global__ void __launch_bounds__(TPB, 4) k32_spmv(Geom g, const TV* __restrict__ val, const float* __restrict__ p,
-                                                   float* __restrict__ w, double* partials, PcgScalars* sc) {
+                                                   float* __restrict__ w, const uint16_t* __restrict__ keep,
+                                                   double* partials, PcgScalars* sc) {
   if (sc_done(sc)) return;
   double v[1] = {0.0};
   const int n = (int)g.n;
   for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
     const int col = row / g.nz;
     const int k = row - col * g.nz;
-    const float wi = row_dot32<MASKC, TV>(g, val, p, row, col, k);
+    const float wi = MASKC >= 0 ? row_dot32_keep<TV>(g, val, p, keep, row, col, k) : row_dot32<MASKC, TV>(g, val, p, row, col, k);
     w[row] = wi;
     v[0] = fma((double)p[row], (double)wi, v[0]);
   }
@@ -1896,7 +1931,8 @@ void inner_iter(pm_operator* op, int which, const TV* val32, bool proj, int prec
   const int G = grid_for(op->n, TPB, op->num_sms);
   {
     KtScope t(PM_KT_SPMV, 1, s);
-    k32_spmv<MASKC, TV><<<G, TPB, 0, s>>>(g, val32, c->p32, c->w32, c->partials, c->sc_in);
+    k32_spmv<MASKC, TV><<<G, TPB, 0, s>>>(g, val32, c->p32, c->w32, MASKC >= 0 ? op->d_keep[MASKC < 0 ? 0 : MASKC] : nullptr,
+                                          c->partials, c->sc_in);
   }
   if (prec == PM_PREC_LINE) {
     {
