@@ -726,9 +726,8 @@ __global__ void __launch_bounds__(LINE_FTPB) k_update_line(Geom g, const double*
 // y_k = t_k w_k and z = U^{-1} y,  (r, z) = y' diag(1/w) y = sum_k t_k y_k.
 constexpr int LINE_WNZ = 32;
 constexpr int LINE_WTPB = 256;   // 8 warps per block
-constexpr int LINE_WBLOCKS = 3;  // resident blocks per SM (8.4 KB of shared memory per warp)
 template <int PROJ, int TCOLS>
-__global__ void __launch_bounds__(LINE_WTPB, LINE_WBLOCKS) k_update_line_w(
+__global__ void __launch_bounds__(LINE_WTPB, TCOLS == 32 ? 3 : 4) k_update_line_w(
     Geom g, const double* __restrict__ F, double* __restrict__ x, double* __restrict__ r,
     const double* __restrict__ p, const double* __restrict__ w, double* __restrict__ z,
     const double* __restrict__ m, double* partials, PcgScalars* sc) {
@@ -817,33 +816,50 @@ __global__ void __launch_bounds__(LINE_WTPB, LINE_WBLOCKS) k_update_line_w(
   }
 }
 
-// Columns per task = lanes: every lane of a warp sweeps a column (an FP64 instruction costs the
-// FP64 pipe the same with idle lanes, and the sweep is a third of the kernel's FP64 work).
+// Columns per task: 32, so that every lane of a warp sweeps a column (an FP64 instruction costs the
+// FP64 pipe the same with idle lanes, and the sweep is a third of the kernel's FP64 work), unless
+// that leaves fewer tasks than resident warps (basins under about 600 x 600 columns of 32 levels):
+// then 16, twice the warps and half the lanes sweeping.
 constexpr int LINE_WCOLS = 32;
 
-// Launch of k_update_line_w: exactly the resident blocks (capped by the partials buffer, 4 lanes
-// per block, and by one task per warp).
-void update_line_w(pm_operator* op, int which, bool proj, double* x, cudaStream_t s) {
+template <int TC>
+int line_w_slots(const void* kernel, int num_sms) {
+  const size_t smem = (size_t)(LINE_WTPB / 32) * TC * (LINE_WNZ + 1) * sizeof(double);
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, LINE_WTPB, smem);
+  return std::max(1, per_sm) * num_sms;
+}
+
+template <int TC>
+void launch_line_w(pm_operator* op, int which, bool proj, double* x, int slots, cudaStream_t s) {
   SolveCtx* c = op->ctx;
   Geom g = geom_of(op);
-  const size_t smem = (size_t)(LINE_WTPB / 32) * LINE_WCOLS * (LINE_WNZ + 1) * sizeof(double);
-  static int slots = 0;
-  if (!slots) {
-    cudaFuncSetAttribute(k_update_line_w<0, LINE_WCOLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_update_line_w<1, LINE_WCOLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_line_w<1, LINE_WCOLS>, LINE_WTPB, smem);
-    slots = std::max(1, per_sm) * op->num_sms;
-  }
+  const size_t smem = (size_t)(LINE_WTPB / 32) * TC * (LINE_WNZ + 1) * sizeof(double);
   int64_t blocks = std::min<int64_t>(slots, (int64_t)NPART * MAX_GRID / 4);
-  const int64_t ntask = (op->ncols + LINE_WCOLS - 1) / LINE_WCOLS;
+  const int64_t ntask = (op->ncols + TC - 1) / TC;
   blocks = std::min<int64_t>(blocks, (ntask + LINE_WTPB / 32 - 1) / (LINE_WTPB / 32));
   const int grid = (int)std::max<int64_t>(1, blocks);
   const double* F = op->d_line[which];
   if (proj)
-    k_update_line_w<1, LINE_WCOLS><<<grid, LINE_WTPB, smem, s>>>(g, F, x, c->r, c->p, c->w, c->z, op->d_m, c->partials, c->sc);
+    k_update_line_w<1, TC><<<grid, LINE_WTPB, smem, s>>>(g, F, x, c->r, c->p, c->w, c->z, op->d_m, c->partials, c->sc);
   else
-    k_update_line_w<0, LINE_WCOLS><<<grid, LINE_WTPB, smem, s>>>(g, F, x, c->r, c->p, c->w, c->z, op->d_m, c->partials, c->sc);
+    k_update_line_w<0, TC><<<grid, LINE_WTPB, smem, s>>>(g, F, x, c->r, c->p, c->w, c->z, op->d_m, c->partials, c->sc);
+}
+
+// Launch of k_update_line_w: exactly the resident blocks (capped by the partials buffer, 4 lanes
+// per block, and by one task per warp).
+void update_line_w(pm_operator* op, int which, bool proj, double* x, cudaStream_t s) {
+  static int slots32 = 0, slots16 = 0;
+  if (!slots32) {
+    slots32 = line_w_slots<32>((const void*)k_update_line_w<1, 32>, op->num_sms);
+    line_w_slots<32>((const void*)k_update_line_w<0, 32>, op->num_sms);
+    slots16 = line_w_slots<16>((const void*)k_update_line_w<1, 16>, op->num_sms);
+    line_w_slots<16>((const void*)k_update_line_w<0, 16>, op->num_sms);
+  }
+  const int64_t tasks32 = (op->ncols + 31) / 32;
+  if (tasks32 >= (int64_t)slots32 * (LINE_WTPB / 32)) launch_line_w<32>(op, which, proj, x, slots32, s);
+  else launch_line_w<16>(op, which, proj, x, slots16, s);
   count_launch();
 }
 
@@ -1378,18 +1394,28 @@ __global__ void k_cvt_diff(int64_t n, int64_t npad, const double* __restrict__ v
 }
 
 template <int MASKC, typename TV>
-__global__ void __launch_bounds__(TPB, 4) k32_spmv(Geom g, const TV* __restrict__ val, const float* __restrict__ p,
+__global__ void __launch_bounds__(TPB, 3) k32_spmv(Geom g, const TV* __restrict__ val, const float* __restrict__ p,
                                                    float* __restrict__ w, const uint16_t* __restrict__ keep,
                                                    double* partials, PcgScalars* sc) {
   if (sc_done(sc)) return;
   double v[1] = {0.0};
   const int n = (int)g.n;
-  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
-    const int col = row / g.nz;
-    const int k = row - col * g.nz;
+  const int stride = gridDim.x * blockDim.x;
+  // two rows per pass (row and row + stride): both rows' loads are in flight together, which the
+  // FP32 kernel needs to cover memory latency (its FP32 arithmetic does not)
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += 2 * stride) {
+    const int row2 = row + stride < n ? row + stride : row;
+    const int col = row / g.nz, k = row - col * g.nz;
+    const int col2 = row2 / g.nz, k2 = row2 - col2 * g.nz;
     const float wi = MASKC >= 0 ? row_dot32_keep<TV>(g, val, p, keep, row, col, k) : row_dot32<MASKC, TV>(g, val, p, row, col, k);
+    const float wi2 = MASKC >= 0 ? row_dot32_keep<TV>(g, val, p, keep, row2, col2, k2)
+                                 : row_dot32<MASKC, TV>(g, val, p, row2, col2, k2);
     w[row] = wi;
     v[0] = fma((double)p[row], (double)wi, v[0]);
+    if (row2 != row) {
+      w[row2] = wi2;
+      v[0] = fma((double)p[row2], (double)wi2, v[0]);
+    }
   }
   if (grid_sum<1>(v, partials, &sc->count[3]) && threadIdx.x == 0) {
     const double pap = v[0];
@@ -1633,19 +1659,19 @@ __global__ void __launch_bounds__(LINE_UCOLS) k32_update_line(Geom g, const floa
   }
 }
 
-// FP32 version of k_update_line_w (32-level columns, warp tasks of 32 columns, no block
+// FP32 version of k_update_line_w (32-level columns, warp tasks of TC columns, no block
 // barriers); the FP32 correction d takes alpha p (folded into the FP64 x at each residual
 // replacement) and the dots are accumulated term by term in FP64. mode as
 // k32_update_line: 0 first step, 1 a full iteration, 2 finish an iteration after a residual
 // replacement. (r, z) = sum_k t_k y_k from the sweep (symmetric column blocks, see
 // k_update_line_w).
-template <int PROJ>
+template <int PROJ, int TC>
 __global__ void __launch_bounds__(LINE_WTPB, 4) k32_update_line_w(Geom g, const float* __restrict__ F,
                                                               float* __restrict__ d, float* __restrict__ r,
                                                               const float* __restrict__ p, const float* __restrict__ w,
                                                               float* __restrict__ z, const double* __restrict__ m,
                                                               double* partials, PcgScalars* sc, int mode) {
-  constexpr int NZ = LINE_WNZ, LD = NZ + 1, TC = LINE_WCOLS;
+  constexpr int NZ = LINE_WNZ, LD = NZ + 1;
   extern __shared__ float smf[];
   const int update = mode == 1;
   if (mode != 0 && sc_done(sc)) return;
@@ -1760,25 +1786,39 @@ void update_line32(pm_operator* op, int which, bool proj, double* x, int mode, c
   SolveCtx* c = op->ctx;
   Geom g = geom_of(op);
   if (op->nz == LINE_WNZ) {
-    const size_t smem = (size_t)(LINE_WTPB / 32) * LINE_WCOLS * (LINE_WNZ + 1) * sizeof(float);
-    static int slots = 0;
-    if (!slots) {
-      cudaFuncSetAttribute(k32_update_line_w<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      cudaFuncSetAttribute(k32_update_line_w<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static int slots32 = 0, slots16 = 0;
+    auto slots_of = [&](const void* kern, int tc) {
+      const size_t sm = (size_t)(LINE_WTPB / 32) * tc * (LINE_WNZ + 1) * sizeof(float);
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       int per_sm = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k32_update_line_w<1>, LINE_WTPB, smem);
-      slots = std::max(1, per_sm) * op->num_sms;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, LINE_WTPB, sm);
+      return std::max(1, per_sm) * op->num_sms;
+    };
+    if (!slots32) {
+      slots32 = slots_of((const void*)k32_update_line_w<1, 32>, 32);
+      slots_of((const void*)k32_update_line_w<0, 32>, 32);
+      slots16 = slots_of((const void*)k32_update_line_w<1, 16>, 16);
+      slots_of((const void*)k32_update_line_w<0, 16>, 16);
     }
-    int64_t blocks = std::min<int64_t>(slots, (int64_t)NPART * MAX_GRID / 4);
-    const int64_t ntask = (op->ncols + LINE_WCOLS - 1) / LINE_WCOLS;
+    // 32-column tasks while they fill the resident warps, else 16 (as update_line_w)
+    const bool wide = (op->ncols + 31) / 32 >= (int64_t)slots32 * (LINE_WTPB / 32);
+    const int tc = wide ? 32 : 16;
+    const size_t smem = (size_t)(LINE_WTPB / 32) * tc * (LINE_WNZ + 1) * sizeof(float);
+    int64_t blocks = std::min<int64_t>(wide ? slots32 : slots16, (int64_t)NPART * MAX_GRID / 4);
+    const int64_t ntask = (op->ncols + tc - 1) / tc;
     blocks = std::min<int64_t>(blocks, (ntask + LINE_WTPB / 32 - 1) / (LINE_WTPB / 32));
     const int grid = (int)std::max<int64_t>(1, blocks);
-    if (proj)
-      k32_update_line_w<1><<<grid, LINE_WTPB, smem, s>>>(g, op->d_line32[which], c->d32, c->r32, c->p32, c->w32, c->z32,
-                                                          op->d_m, c->partials, c->sc_in, mode);
-    else
-      k32_update_line_w<0><<<grid, LINE_WTPB, smem, s>>>(g, op->d_line32[which], c->d32, c->r32, c->p32, c->w32, c->z32,
-                                                          op->d_m, c->partials, c->sc_in, mode);
+#define PM_UL32(P, TCV)                                                                                   \
+  k32_update_line_w<P, TCV><<<grid, LINE_WTPB, smem, s>>>(g, op->d_line32[which], c->d32, c->r32, c->p32, c->w32, \
+                                                           c->z32, op->d_m, c->partials, c->sc_in, mode)
+    if (wide) {
+      if (proj) PM_UL32(1, 32);
+      else PM_UL32(0, 32);
+    } else {
+      if (proj) PM_UL32(1, 16);
+      else PM_UL32(0, 16);
+    }
+#undef PM_UL32
     return;
   }
   const int64_t ntiles = (op->ncols + LINE_UCOLS - 1) / LINE_UCOLS;
