@@ -65,6 +65,7 @@ static void free_operator(pm_operator* op) {
   cudaFree(op->d_coriolis);
   cudaFree(op->d_cls_cols);
   cudaFree(op->d_struct);
+  cudaFree(op->d_m2f);
   for (int c = 0; c < 3; ++c) cudaFree(op->d_keep[c]);
   cudaFree(op->d_m);
   for (int v = 0; v < VS_COUNT; ++v) {

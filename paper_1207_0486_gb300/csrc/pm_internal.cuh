@@ -219,6 +219,7 @@ struct pm_operator {
   float* d_val32[pm::VS_COUNT] = {};
   uint16_t* d_val16[pm::VS_COUNT] = {};  // bf16 bit patterns
   double* d_m = nullptr;            // M 1
+  float2* d_m2f = nullptr;          // M 1 split into two floats (mixed-precision kernels)
   double* d_dinv[8] = {};           // Jacobi inverse diagonals per (op, mask)
   float* d_dinv32[8] = {};
   pm::Ic0Factor ic0[8];

@@ -1286,6 +1286,37 @@ int pcg_run(pm_operator* op, int which, const double* b, double* x, const pm_sol
 // FP32 SpMV / preconditioner arithmetic, FP64 dot products and alpha / beta, to a relative
 // reduction inner_rtol; then x += d in FP64.
 
+// Compensated FP32 ("double-float") accumulation of the mixed-precision dot products. GB300's
+// FP64 pipe runs at 1/64 of its FP32 rate, and an FP64 dot of FP32 vectors costs two conversions
+// and an FP64 FMA per term on that pipe, which made the FP32 kernels FP64-bound. Here each product
+// a b is split exactly into p + e by one FP32 FMA (TwoProduct), p is added to the running sum by
+// TwoSum, and both rounding errors go into a second FP32 word: a thread's partial sum keeps about
+// 48 significant bits (relative error of order n u32^2 for its n terms, u32 = 2^-24) and becomes
+// an FP64 number once, where the FP64 block and grid reductions take over.
+struct DF {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float a) {
+    const float s = __fadd_rn(hi, a);
+    const float bv = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(a, bv));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float pr = __fmul_rn(a, b);
+    const float pe = fmaf(a, b, -pr);
+    add(pr);
+    lo = __fadd_rn(lo, pe);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// m'z with m held exactly as two floats (hi + lo = m in FP64 to 48 bits) for the FP32 kernels.
+__device__ __forceinline__ void add_mz(DF& acc, float2 m2, float z) {
+  acc.add_prod(m2.x, z);
+  acc.add_prod(m2.y, z);
+}
+
 __device__ __forceinline__ float ldv(const float* p, int i) { return __ldg(p + i); }
 __device__ __forceinline__ float ldv(const __nv_bfloat16* p, int i) { return __bfloat162float(p[i]); }
 
@@ -1394,29 +1425,21 @@ __global__ void k_cvt_diff(int64_t n, int64_t npad, const double* __restrict__ v
 }
 
 template <int MASKC, typename TV>
-__global__ void __launch_bounds__(TPB, 3) k32_spmv(Geom g, const TV* __restrict__ val, const float* __restrict__ p,
+__global__ void __launch_bounds__(TPB, 4) k32_spmv(Geom g, const TV* __restrict__ val, const float* __restrict__ p,
                                                    float* __restrict__ w, const uint16_t* __restrict__ keep,
                                                    double* partials, PcgScalars* sc) {
   if (sc_done(sc)) return;
   double v[1] = {0.0};
+  DF a0;
   const int n = (int)g.n;
-  const int stride = gridDim.x * blockDim.x;
-  // two rows per pass (row and row + stride): both rows' loads are in flight together, which the
-  // FP32 kernel needs to cover memory latency (its FP32 arithmetic does not)
-  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += 2 * stride) {
-    const int row2 = row + stride < n ? row + stride : row;
-    const int col = row / g.nz, k = row - col * g.nz;
-    const int col2 = row2 / g.nz, k2 = row2 - col2 * g.nz;
+  for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
+    const int col = row / g.nz;
+    const int k = row - col * g.nz;
     const float wi = MASKC >= 0 ? row_dot32_keep<TV>(g, val, p, keep, row, col, k) : row_dot32<MASKC, TV>(g, val, p, row, col, k);
-    const float wi2 = MASKC >= 0 ? row_dot32_keep<TV>(g, val, p, keep, row2, col2, k2)
-                                 : row_dot32<MASKC, TV>(g, val, p, row2, col2, k2);
     w[row] = wi;
-    v[0] = fma((double)p[row], (double)wi, v[0]);
-    if (row2 != row) {
-      w[row2] = wi2;
-      v[0] = fma((double)p[row2], (double)wi2, v[0]);
-    }
+    a0.add_prod(p[row], wi);
   }
+  v[0] = a0.value();
   if (grid_sum<1>(v, partials, &sc->count[3]) && threadIdx.x == 0) {
     const double pap = v[0];
     sc->pAp = pap;
@@ -1434,26 +1457,27 @@ __global__ void __launch_bounds__(TPB, 3) k32_spmv(Geom g, const TV* __restrict_
 template <int PROJ, int INLINE_Z>
 __global__ void __launch_bounds__(TPB) k32_update(int64_t n, float* __restrict__ d, float* __restrict__ r,
                                                   const float* __restrict__ p, const float* __restrict__ w,
-                                                  const float* __restrict__ dinv, const double* __restrict__ m,
+                                                  const float* __restrict__ dinv, const float2* __restrict__ m2,
                                                   double* partials, PcgScalars* sc) {
   if (sc_done(sc)) return;
   const double alpha_d = sc->alpha;
   const float alpha = (float)alpha_d;
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  DF a[4];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     d[i] = fmaf(alpha, p[i], d[i]);
     const float ri = fmaf(-alpha, w[i], r[i]);
     r[i] = ri;
-    v[0] = fma((double)ri, (double)ri, v[0]);
+    a[0].add_prod(ri, ri);
     if (INLINE_Z) {
       const float zi = dinv[i] * ri;
-      v[1] = fma((double)ri, (double)zi, v[1]);
+      a[1].add_prod(ri, zi);
       if (PROJ) {
-        v[2] = fma(m[i], (double)zi, v[2]);
-        v[3] += (double)ri;
+        add_mz(a[2], m2[i], zi);
+        a[3].add(ri);
       }
     }
   }
+  double v[4] = {a[0].value(), a[1].value(), a[2].value(), a[3].value()};
   if (grid_sum<4>(v, partials, &sc->count[4]) && threadIdx.x == 0) {
     sc->iter += 1;
     sc->rr = v[0];
@@ -1481,19 +1505,20 @@ __global__ void __launch_bounds__(TPB) k32_update(int64_t n, float* __restrict__
 // rho = (r, z') with z' = z - c (pressure) from stored or inline z; first: beta = 0.
 template <int PROJ, int STORED>
 __global__ void __launch_bounds__(TPB) k32_rho(int64_t n, const float* __restrict__ r, const float* __restrict__ dinv,
-                                               const float* __restrict__ zbuf, const double* __restrict__ m,
+                                               const float* __restrict__ zbuf, const float2* __restrict__ m2,
                                                double* partials, PcgScalars* sc, int is_first) {
   if (!is_first && sc_done(sc)) return;
-  double v[3] = {0.0, 0.0, 0.0};
+  DF a[3];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float ri = r[i];
     const float zi = STORED ? zbuf[i] : dinv[i] * ri;
-    v[0] = fma((double)ri, (double)zi, v[0]);
+    a[0].add_prod(ri, zi);
     if (PROJ) {
-      v[1] = fma(m[i], (double)zi, v[1]);
-      v[2] += (double)ri;
+      add_mz(a[1], m2[i], zi);
+      a[2].add(ri);
     }
   }
+  double v[3] = {a[0].value(), a[1].value(), a[2].value()};
   if (grid_sum<3>(v, partials, &sc->count[2]) && threadIdx.x == 0) {
     const double c = PROJ ? v[1] / sc->one_m : 0.0;
     const double rho_new = v[0] - c * v[2];
@@ -1521,6 +1546,14 @@ __global__ void __launch_bounds__(TPB) k32_pupd(int64_t n, const float* __restri
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float zi = (STORED ? zbuf[i] : dinv[i] * r[i]) - c;
     p[i] = is_first ? zi : fmaf(beta, p[i], zi);
+  }
+}
+
+// m = hi + lo as two floats (hi = fl32(m), lo = fl32(m - hi)) for the FP32 kernels' m'z.
+__global__ void k_split_m(int64_t n, const double* __restrict__ m, float2* __restrict__ m2) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float hi = (float)m[i];
+    m2[i] = make_float2(hi, (float)(m[i] - (double)hi));
   }
 }
 
@@ -1554,7 +1587,7 @@ template <int PROJ>
 __global__ void __launch_bounds__(LINE_UCOLS) k32_update_line(Geom g, const float* __restrict__ F,
                                                             float* __restrict__ d, float* __restrict__ r,
                                                             const float* __restrict__ p, const float* __restrict__ w,
-                                                            float* __restrict__ z, const double* __restrict__ m,
+                                                            float* __restrict__ z, const float2* __restrict__ m2,
                                                             double* partials, PcgScalars* sc, int mode) {
   // mode 0: first step (z, rho, beta = 0); 1: a full iteration (d, r update, z, rho, beta);
   // 2: finish an iteration after a residual replacement (z, rho_new, beta = rho_new / rho)
@@ -1567,7 +1600,7 @@ __global__ void __launch_bounds__(LINE_UCOLS) k32_update_line(Geom g, const floa
   const int ncols = g.ncols;
   const int n = (int)g.n;
   const int ntiles = (ncols + LINE_UCOLS - 1) / LINE_UCOLS;
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  DF a[4];
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int c0 = tile * LINE_UCOLS;
     const int cc = min(LINE_UCOLS, ncols - c0);
@@ -1582,7 +1615,7 @@ __global__ void __launch_bounds__(LINE_UCOLS) k32_update_line(Geom g, const floa
         r[row] = ri;
       }
       smf[(i / nz) * ld + i % nz] = ri;
-      v[0] = fma((double)ri, (double)ri, v[0]);
+      a[0].add_prod(ri, ri);
     }
     __syncthreads();
     if ((int)threadIdx.x < cc) {
@@ -1609,14 +1642,15 @@ __global__ void __launch_bounds__(LINE_UCOLS) k32_update_line(Geom g, const floa
       const float zi = smf[(i / nz) * ld + i % nz];
       const float ri = r[row];
       z[row] = zi;
-      v[1] = fma((double)ri, (double)zi, v[1]);
+      a[1].add_prod(ri, zi);
       if (PROJ) {
-        v[2] = fma(m[row], (double)zi, v[2]);
-        v[3] += (double)ri;
+        add_mz(a[2], m2[row], zi);
+        a[3].add(ri);
       }
     }
     __syncthreads();
   }
+  double v[4] = {a[0].value(), a[1].value(), a[2].value(), a[3].value()};
   if (grid_sum<4>(v, partials, &sc->count[4]) && threadIdx.x == 0) {
     const double c = PROJ ? v[2] / sc->one_m : 0.0;
     const double rho_new = v[1] - c * v[3];
@@ -1669,7 +1703,7 @@ template <int PROJ, int TC>
 __global__ void __launch_bounds__(LINE_WTPB, 4) k32_update_line_w(Geom g, const float* __restrict__ F,
                                                               float* __restrict__ d, float* __restrict__ r,
                                                               const float* __restrict__ p, const float* __restrict__ w,
-                                                              float* __restrict__ z, const double* __restrict__ m,
+                                                              float* __restrict__ z, const float2* __restrict__ m2,
                                                               double* partials, PcgScalars* sc, int mode) {
   constexpr int NZ = LINE_WNZ, LD = NZ + 1;
   extern __shared__ float smf[];
@@ -1687,7 +1721,7 @@ __global__ void __launch_bounds__(LINE_WTPB, 4) k32_update_line_w(Geom g, const 
   const int ntask = (ncols + TC - 1) / TC;
   const int tbeg = (int)((int64_t)ntask * wg / nwarps);
   const int tend = (int)((int64_t)ntask * (wg + 1) / nwarps);
-  double v[4] = {0.0, 0.0, 0.0, 0.0};   // (r, r), (r, z), m'z, 1'r
+  DF a[4];   // (r, r), (r, z), m'z, 1'r
   for (int t = tbeg; t < tend; ++t) {
     const int c0 = t * TC;
     const int cc = min(TC, ncols - c0);
@@ -1702,21 +1736,20 @@ __global__ void __launch_bounds__(LINE_WTPB, 4) k32_update_line_w(Geom g, const 
         r[row] = ri;
       }
       ws[j * LD + lane] = ri;
-      v[0] = fma((double)ri, (double)ri, v[0]);
-      if (PROJ) v[3] += (double)ri;
+      a[0].add_prod(ri, ri);
+      if (PROJ) a[3].add(ri);
     }
     __syncwarp();
     if (lane < cc) {
       const int col = c0 + lane;
       float* cs = ws + lane * LD;
       float y = 0.f;
-      double rz = 0.0;
 #pragma unroll 8
       for (int k = 0; k < NZ; ++k) {
         const int li = k * ncols + col;
         const float tk = fmaf(-F[li], y, cs[k]);
         y = tk * F[n + li];
-        rz = fma((double)tk, (double)y, rz);
+        a[1].add_prod(tk, y);
         cs[k] = y;
       }
       float zn = y;
@@ -1726,7 +1759,6 @@ __global__ void __launch_bounds__(LINE_WTPB, 4) k32_update_line_w(Geom g, const 
         zn = fmaf(-F[2 * n + li], zn, cs[k]);
         cs[k] = zn;
       }
-      v[1] += rz;
     }
     __syncwarp();
 #pragma unroll 8
@@ -1734,10 +1766,11 @@ __global__ void __launch_bounds__(LINE_WTPB, 4) k32_update_line_w(Geom g, const 
       const int row = row0 + j * NZ;
       const float zi = ws[j * LD + lane];
       z[row] = zi;
-      if (PROJ) v[2] = fma(m[row], (double)zi, v[2]);
+      if (PROJ) add_mz(a[2], m2[row], zi);
     }
     __syncwarp();
   }
+  double v[4] = {a[0].value(), a[1].value(), a[2].value(), a[3].value()};
   if (grid_sum<4>(v, partials, &sc->count[4]) && threadIdx.x == 0) {
     const double c = PROJ ? v[2] / sc->one_m : 0.0;
     const double rho_new = v[1] - c * v[3];
@@ -1810,7 +1843,7 @@ void update_line32(pm_operator* op, int which, bool proj, double* x, int mode, c
     const int grid = (int)std::max<int64_t>(1, blocks);
 #define PM_UL32(P, TCV)                                                                                   \
   k32_update_line_w<P, TCV><<<grid, LINE_WTPB, smem, s>>>(g, op->d_line32[which], c->d32, c->r32, c->p32, c->w32, \
-                                                           c->z32, op->d_m, c->partials, c->sc_in, mode)
+                                                           c->z32, op->d_m2f, c->partials, c->sc_in, mode)
     if (wide) {
       if (proj) PM_UL32(1, 32);
       else PM_UL32(0, 32);
@@ -1826,10 +1859,10 @@ void update_line32(pm_operator* op, int which, bool proj, double* x, int mode, c
   const size_t smem = (size_t)LINE_UCOLS * (op->nz + 1) * sizeof(float);
   if (proj)
     k32_update_line<1><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], c->d32, c->r32, c->p32, c->w32, c->z32,
-                                                      op->d_m, c->partials, c->sc_in, mode);
+                                                      op->d_m2f, c->partials, c->sc_in, mode);
   else
     k32_update_line<0><<<grid, LINE_UCOLS, smem, s>>>(g, op->d_line32[which], c->d32, c->r32, c->p32, c->w32, c->z32,
-                                                      op->d_m, c->partials, c->sc_in, mode);
+                                                      op->d_m2f, c->partials, c->sc_in, mode);
 }
 
 // FP32 IC0 colour sweep (as k_ic0_sweep).
@@ -1903,6 +1936,13 @@ int ensure_mixed(pm_operator* op, int which, int precision, int prec, cudaStream
     e = e ? e : cudaMallocHost((void**)&c->sc_in_host, sizeof(PcgScalars));
     if (e != cudaSuccess) return cuda_check(e, "mixed-precision workspace");
     op->device_bytes += 5 * (int64_t)fb;
+  }
+  if (!op->d_m2f) {
+    int st = cuda_check(cudaMalloc((void**)&op->d_m2f, (size_t)op->n * sizeof(float2)), "cudaMalloc m split");
+    if (st) return st;
+    op->device_bytes += op->n * 8;
+    k_split_m<<<grid_for(op->n, TPB, op->num_sms), TPB, 0, s>>>(op->n, op->d_m, op->d_m2f);
+    count_launch();
   }
   const int vs = which_valset(which);
   const int64_t nv = (int64_t)NSLOT * op->npad;
@@ -1987,7 +2027,7 @@ void inner_iter(pm_operator* op, int which, const TV* val32, bool proj, int prec
   } else if (prec == PM_PREC_IC0) {
     {
       KtScope t(PM_KT_UPDATE, 1, s);
-      k32_update<0, 0><<<G, TPB, 0, s>>>(op->n, c->d32, c->r32, c->p32, c->w32, dinv32, op->d_m, c->partials, c->sc_in);
+      k32_update<0, 0><<<G, TPB, 0, s>>>(op->n, c->d32, c->r32, c->p32, c->w32, dinv32, op->d_m2f, c->partials, c->sc_in);
     }
     {
       KtScope t(PM_KT_IC0, 16, s);
@@ -1995,16 +2035,16 @@ void inner_iter(pm_operator* op, int which, const TV* val32, bool proj, int prec
     }
     {
       KtScope t(PM_KT_PUPDATE, 2, s);
-      if (proj) k32_rho<1, 1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, op->d_m, c->partials, c->sc_in, 0);
-      else k32_rho<0, 1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, op->d_m, c->partials, c->sc_in, 0);
+      if (proj) k32_rho<1, 1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, op->d_m2f, c->partials, c->sc_in, 0);
+      else k32_rho<0, 1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, op->d_m2f, c->partials, c->sc_in, 0);
       k32_pupd<1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, c->p32, c->sc_in, 0);
     }
     count_launch(4);
   } else {
     {
       KtScope t(PM_KT_UPDATE, 1, s);
-      if (proj) k32_update<1, 1><<<G, TPB, 0, s>>>(op->n, c->d32, c->r32, c->p32, c->w32, dinv32, op->d_m, c->partials, c->sc_in);
-      else k32_update<0, 1><<<G, TPB, 0, s>>>(op->n, c->d32, c->r32, c->p32, c->w32, dinv32, op->d_m, c->partials, c->sc_in);
+      if (proj) k32_update<1, 1><<<G, TPB, 0, s>>>(op->n, c->d32, c->r32, c->p32, c->w32, dinv32, op->d_m2f, c->partials, c->sc_in);
+      else k32_update<0, 1><<<G, TPB, 0, s>>>(op->n, c->d32, c->r32, c->p32, c->w32, dinv32, op->d_m2f, c->partials, c->sc_in);
     }
     {
       KtScope t(PM_KT_PUPDATE, 1, s);
@@ -2027,12 +2067,12 @@ void inner_first(pm_operator* op, int which, bool proj, int prec, const float* d
       k32_pupd<1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, c->p32, c->sc_in, 0);
     } else if (prec == PM_PREC_IC0) {
       ic0_apply32(op, which, c->r32, c->z32, c->sc_in, 0, s);
-      if (proj) k32_rho<1, 1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, op->d_m, c->partials, c->sc_in, 0);
-      else k32_rho<0, 1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, op->d_m, c->partials, c->sc_in, 0);
+      if (proj) k32_rho<1, 1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, op->d_m2f, c->partials, c->sc_in, 0);
+      else k32_rho<0, 1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, op->d_m2f, c->partials, c->sc_in, 0);
       k32_pupd<1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, c->p32, c->sc_in, 0);
     } else {
-      if (proj) k32_rho<1, 0><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, nullptr, op->d_m, c->partials, c->sc_in, 0);
-      else k32_rho<0, 0><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, nullptr, op->d_m, c->partials, c->sc_in, 0);
+      if (proj) k32_rho<1, 0><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, nullptr, op->d_m2f, c->partials, c->sc_in, 0);
+      else k32_rho<0, 0><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, nullptr, op->d_m2f, c->partials, c->sc_in, 0);
       k32_pupd<0><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, nullptr, c->p32, c->sc_in, 0);
     }
     count_launch(2);
@@ -2043,12 +2083,12 @@ void inner_first(pm_operator* op, int which, bool proj, int prec, const float* d
     k32_pupd<1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, c->p32, c->sc_in, 1);
   } else if (prec == PM_PREC_IC0) {
     ic0_apply32(op, which, c->r32, c->z32, c->sc_in, 0, s);
-    if (proj) k32_rho<1, 1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, op->d_m, c->partials, c->sc_in, 1);
-    else k32_rho<0, 1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, op->d_m, c->partials, c->sc_in, 1);
+    if (proj) k32_rho<1, 1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, op->d_m2f, c->partials, c->sc_in, 1);
+    else k32_rho<0, 1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, op->d_m2f, c->partials, c->sc_in, 1);
     k32_pupd<1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, c->p32, c->sc_in, 1);
   } else {
-    if (proj) k32_rho<1, 0><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, nullptr, op->d_m, c->partials, c->sc_in, 1);
-    else k32_rho<0, 0><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, nullptr, op->d_m, c->partials, c->sc_in, 1);
+    if (proj) k32_rho<1, 0><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, nullptr, op->d_m2f, c->partials, c->sc_in, 1);
+    else k32_rho<0, 0><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, nullptr, op->d_m2f, c->partials, c->sc_in, 1);
     k32_pupd<0><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, nullptr, c->p32, c->sc_in, 1);
   }
   count_launch(2);
