@@ -253,23 +253,49 @@ def roofline_of(kt, n, steps, ms_total, peak, peak_kind, sm_mhz=None):
     return out
 
 
+def kernel_source_hash(path: str, names) -> str:
+    """sha256[:12] of the source text of the named device functions (each from its name at a
+    definition to the matching closing brace), so that a traffic figure follows the kernel's own
+    code rather than the whole file."""
+    import hashlib
+    import re
+    with open(path) as fh:
+        src = fh.read()
+    parts = []
+    for name in names:
+        m = None
+        for cand in re.finditer(r"\b" + re.escape(name) + r"\s*\(", src):
+            head = src[max(0, cand.start() - 400):cand.start()]
+            if "__global__" in head.split(";")[-1] or "__device__" in head.split(";")[-1]:
+                m = cand
+                break
+        if m is None:
+            raise ValueError(f"{name} not found in {path}")
+        k = src.index("{", m.end())
+        depth = 0
+        for e in range(k, len(src)):
+            depth += {"{": 1, "}": -1}.get(src[e], 0)
+            if depth == 0:
+                break
+        parts.append(src[m.start():e + 1])
+    return hashlib.sha256("\n".join(parts).encode()).hexdigest()[:12]
+
+
 def dram_traffic(kernel: str):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of `kernel` from the
-    ncu summary in profiles/traffic.md, or None when the source file the counters were taken on
-    has changed since (its sha256 prefix is recorded next to the figure)."""
-    import hashlib
+    ncu summary in profiles/traffic.md, or None when the kernel's source (the functions listed
+    beside the figure) has changed since the counters were taken (its hash is recorded there)."""
     path = os.path.join(ROOT, "profiles", "traffic.md")
     if not os.path.exists(path):
         return None
     with open(path) as fh:
         for line in fh:
             cells = [c.strip() for c in line.strip().strip("|").split("|")]
-            if len(cells) >= 4 and cells[0] == f"`{kernel}`":
+            if len(cells) >= 5 and cells[0] == f"`{kernel}`":
                 src = os.path.join(ROOT, "paper_1207_0486_gb300", "csrc", cells[2])
+                names = [n.strip().strip("`") for n in cells[3].split(",")]
                 try:
-                    with open(src, "rb") as sf:
-                        digest = hashlib.sha256(sf.read()).hexdigest()[:12]
-                    return int(cells[1]) if digest == cells[3] else None
+                    return int(cells[1]) if kernel_source_hash(src, names) == cells[4] else None
                 except (OSError, ValueError):
                     return None
     return None

@@ -45,18 +45,25 @@ def test_traffic_lookup(tmp_path, monkeypatch):
     import bench
     src_dir = tmp_path / "paper_1207_0486_gb300" / "csrc"
     src_dir.mkdir(parents=True)
-    (src_dir / "k.cu").write_text("// kernel\n")
-    import hashlib
-    digest = hashlib.sha256(b"// kernel\n").hexdigest()[:12]
+    (src_dir / "k.cu").write_text("// kernels\n__global__ void k_a(int x) {\n  if (x) { x = 1; }\n}\n"
+                                  "__device__ int helper(int y) { return y; }\n")
+    digest = bench.kernel_source_hash(str(src_dir / "k.cu"), ["k_a", "helper"])
     prof = tmp_path / "profiles"
     prof.mkdir()
     (prof / "traffic.md").write_text(
-        "| kernel | bytes | file | sha |\n|---|---|---|---|\n"
-        f"| `k_a` | 1234 | k.cu | {digest} |\n| `k_b` | 99 | k.cu | 000000000000 |\n")
+        "| kernel | bytes | file | functions | sha |\n|---|---|---|---|---|\n"
+        f"| `k_a` | 1234 | k.cu | `k_a`, `helper` | {digest} |\n| `k_b` | 99 | k.cu | `k_a` | 000000000000 |\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.dram_traffic("k_a") == 1234
     assert bench.dram_traffic("k_b") is None   # source changed since the capture
     assert bench.dram_traffic("k_c") is None   # not captured
+    # an edit elsewhere in the file keeps the figure; an edit inside a listed function drops it
+    (src_dir / "k.cu").write_text("// kernels, edited comment\n__global__ void k_a(int x) {\n  if (x) { x = 1; }\n}\n"
+                                  "__device__ int helper(int y) { return y; }\n")
+    assert bench.dram_traffic("k_a") == 1234
+    (src_dir / "k.cu").write_text("__global__ void k_a(int x) {\n  if (x) { x = 2; }\n}\n"
+                                  "__device__ int helper(int y) { return y; }\n")
+    assert bench.dram_traffic("k_a") is None
 
 
 def test_roofline_of_dominant_class():
