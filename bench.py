@@ -474,6 +474,38 @@ def _step_stats(stats):
             "solves_with_work": sum(1 for s in stats[:4] if s.iters > 0)}
 
 
+def run_resident_leg(args):
+    """A fixed load on the resident solve server, for timing and profiling its persistent kernel:
+    `--systems` copies of one box basin's pressure (or velocity) system kept resident and run for
+    `--quanta` launches of `--quantum` iterations, with a tolerance out of reach so that every
+    system stays active. Prints microseconds per iteration of the timed launches."""
+    import torch
+
+    import paper_1207_0486_gb300 as pm
+    from workloads import box_basin, random_vector
+
+    torch.cuda.set_device(0)
+    op = pm.assemble_operator(box_basin(nh=args.nh, nz=args.nz))
+    prc = pm.FP32_REFINE if args.precision == "fp32" else pm.FP64
+    srv = pm.Server(slots=max(args.systems, 1), nz_cap=max(args.nz, 2),
+                    opts=pm.Options(rtol=1e-300, prec=pm.PREC_LINE, precision=prc, max_iter=10 ** 8,
+                                    inner_rtol=1e-2), tile_cols=64, block=128)
+    b = torch.from_numpy(random_vector(op.n, 1207)).cuda()
+    xs = [torch.zeros(op.n, dtype=torch.float64, device="cuda") for _ in range(args.systems)]
+    ws = [torch.empty(srv.workspace_bytes(op), dtype=torch.uint8, device="cuda") for _ in range(args.systems)]
+    for k in range(args.systems):
+        srv.admit(op, args.which, b, xs[k], ws[k])
+    srv.run(1)
+    t0 = time.perf_counter()
+    active = [srv.run(args.quantum) for _ in range(args.quanta)]
+    us = (time.perf_counter() - t0) / (args.quanta * args.quantum) * 1e6
+    srv.close()
+    op.close()
+    print(json.dumps({"resident_load": {"systems": args.systems, "basin": f"box{args.nh}x{args.nh}x{args.nz}",
+                                        "which": args.which, "precision": args.precision,
+                                        "us_per_iteration": round(us, 1), "active": min(active)}}))
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -765,6 +797,15 @@ def main():
     ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--cpu-worker", action="store_true")
+    ap.add_argument("--resident-load", action="store_true",
+                    help="time a fixed load on the resident solve server (see run_resident_leg)")
+    ap.add_argument("--systems", type=int, default=9)
+    ap.add_argument("--nh", type=int, default=100)
+    ap.add_argument("--nz", type=int, default=30)
+    ap.add_argument("--which", type=int, default=3, help="resident load: 0-2 velocity component, 3 pressure")
+    ap.add_argument("--quanta", type=int, default=3)
+    ap.add_argument("--quantum", type=int, default=8)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--nx", type=int, default=512,
                     help="basin columns per side (512 = the benchmark workload; smaller for profiling)")
     args = ap.parse_args()
@@ -773,6 +814,9 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.resident_load:
+        run_resident_leg(args)
         return
     run_ours(args)
 

@@ -116,7 +116,17 @@ typedef struct pm_solve_opts {
   int32_t x0_is_guess;   /* 1: x holds the initial guess; 0: start from x = 0               */
   int32_t max_restarts;  /* true-residual restarts after the recursive test passes (FP64)   */
   double inner_rtol;     /* mixed precision: relative reduction asked of each inner solve  */
+  int32_t kernel;        /* FP64 solves: PM_KERNEL_AUTO (resident for n <= 16384 rows),
+                            PM_KERNEL_STREAM (one launch per PCG phase, every SM), or
+                            PM_KERNEL_RESIDENT (one block runs the whole solve, n <= 2^20)   */
+  int32_t pad;
 } pm_solve_opts;
+
+/* How an FP64 solve runs on the GPU (no paper counterpart; the iterates are those of the Section 5
+ * PCG either way). STREAM issues one kernel per phase of every PCG iteration over the whole GPU;
+ * RESIDENT runs the whole solve in one block of one SM, with block barriers between phases and one
+ * read-back at the end: for small systems, whose stream iterations are bound by launch latency. */
+enum { PM_KERNEL_AUTO = 0, PM_KERNEL_STREAM = 1, PM_KERNEL_RESIDENT = 2 };
 
 typedef struct pm_solve_stats {
   int32_t iters;              /* PCG iterations (summed over restarts / inner solves)       */

@@ -12,7 +12,7 @@ from .api import (  # noqa: F401
     OP_GRAD_X, OP_GRAD_Y, OP_GRAD_Z, PREC_JACOBI, PREC_IC0, PREC_NONE, PREC_LINE, FP64, FP32_REFINE,
     BF16_REFINE, STEP_LUMPED, STEP_CONSISTENT, SLOT_OFFSETS, NBR_OFFSETS,
     FIELD_U1, FIELD_U2, FIELD_U3, FIELD_U1_PREV, FIELD_U2_PREV, FIELD_U3_PREV, FIELD_P, FIELD_Q,
-    FIELD_UT1, FIELD_UT2, FIELD_UT3, FIELD_BP, DIAG_NAMES,
+    FIELD_UT1, FIELD_UT2, FIELD_UT3, FIELD_BP, DIAG_NAMES, KERNEL_AUTO, KERNEL_STREAM, KERNEL_RESIDENT,
     PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_NOT_CONVERGED, PM_BREAKDOWN, PM_TIMEOUT,
     PM_DISCONNECTED, PM_EBUSY,
 )

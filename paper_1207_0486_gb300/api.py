@@ -24,6 +24,7 @@ OP_VEL1_U1, OP_VEL1_U2, OP_VEL1_U3, OP_GRAD_X, OP_GRAD_Y, OP_GRAD_Z = 5, 6, 7, 8
 PREC_JACOBI, PREC_IC0, PREC_NONE, PREC_LINE = 0, 1, 2, 3
 FP64, FP32_REFINE, BF16_REFINE = 0, 1, 2
 STEP_LUMPED, STEP_CONSISTENT = 0, 1
+KERNEL_AUTO, KERNEL_STREAM, KERNEL_RESIDENT = 0, 1, 2
 (FIELD_U1, FIELD_U2, FIELD_U3, FIELD_U1_PREV, FIELD_U2_PREV, FIELD_U3_PREV, FIELD_P, FIELD_Q,
  FIELD_UT1, FIELD_UT2, FIELD_UT3, FIELD_BP) = range(12)
 DIAG_KINETIC_ENERGY, DIAG_DIV_U, DIAG_DIV_UT, DIAG_P_MEAN, DIAG_COUNT = range(5)
@@ -49,7 +50,8 @@ class Physics(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("prec", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("x0_is_guess", ctypes.c_int32),
-                ("max_restarts", ctypes.c_int32), ("inner_rtol", ctypes.c_double)]
+                ("max_restarts", ctypes.c_int32), ("inner_rtol", ctypes.c_double),
+                ("kernel", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class SolveStats(ctypes.Structure):
@@ -202,10 +204,11 @@ class Options:
     x0_is_guess: bool = False
     max_restarts: int = 3
     inner_rtol: float = 1e-4
+    kernel: int = 0            # KERNEL_AUTO, KERNEL_STREAM, KERNEL_RESIDENT
 
     def c(self) -> SolveOpts:
         return SolveOpts(self.rtol, self.max_iter, self.prec, self.precision, int(self.x0_is_guess),
-                         self.max_restarts, self.inner_rtol)
+                         self.max_restarts, self.inner_rtol, self.kernel, 0)
 
 
 class Operator:

@@ -39,6 +39,8 @@ struct SolveCtx {
   float *r32 = nullptr, *p32 = nullptr, *w32 = nullptr, *z32 = nullptr, *d32 = nullptr;
   PcgScalars* sc_in = nullptr;
   PcgScalars* sc_in_host = nullptr;
+  void* small_out = nullptr;        // SmallOut of the resident solve (device)
+  void* small_out_host = nullptr;   // pinned host copy
 };
 
 struct ColourMap;  // pm_assemble.cu
@@ -460,39 +462,44 @@ struct CMap {
 // Forward (FWD = 1): y_i = (r_i - sum_{colour(j) < c} L_ij y_j) / L_ii over rows of colour c.
 // Backward (FWD = 0): z_i = (y_i - sum_{colour(j) > c} L_ji z_j) / L_ii, in place on y.
 // The factor's diagonal slot holds 1 / L_ii (a multiply instead of an FP64 division).
+// Position t of colour COLOUR: column cls_cols[cls_off + t / nlev], level 2 (t % nlev) + parity.
+template <int COLOUR, int FWD>
+__device__ __forceinline__ void ic0_row(const Geom& g, const CMap& cm, const int32_t* __restrict__ cls_cols,
+                                        int64_t cls_off, int64_t t, const double* __restrict__ F,
+                                        const double* __restrict__ r, double* __restrict__ y) {
+  constexpr int kpar = COLOUR >> 2;
+  const int nlev = cm.nlev[kpar];
+  const int nz = g.nz;
+  const int col = __ldg(cls_cols + cls_off + t / nlev);
+  const int k = 2 * (int)(t % nlev) + kpar;
+  const int64_t row = (int64_t)col * nz + k;
+  const int64_t pi = cm.cbase[COLOUR] + t;
+  double acc = FWD ? r[row] : y[row];
+#pragma unroll
+  for (int s = 0; s < NSLOT; ++s) {
+    if (s == DIAG_SLOT) continue;
+    const int cj = COLOUR ^ slot_flip(s);
+    if (FWD ? (cj > COLOUR) : (cj < COLOUR)) continue;
+    const int q = slot_q(s);
+    const int kk = k + slot_dk(s);
+    if (kk < 0 || kk >= nz) continue;
+    const int nb = q == 0 ? col : __ldg(g.nbr + (int64_t)col * NNBR + q);
+    if (nb < 0) continue;
+    acc = fma(-F[(int64_t)s * g.n + pi], y[(int64_t)nb * nz + kk], acc);
+  }
+  y[row] = acc * F[(int64_t)DIAG_SLOT * g.n + pi];
+}
+
 template <int COLOUR, int FWD>
 __global__ void __launch_bounds__(TPB) k_ic0_sweep(Geom g, CMap cm, const int32_t* __restrict__ cls_cols,
                                                    int64_t cls_off, int64_t cls_cnt, const double* __restrict__ F,
                                                    const double* __restrict__ r, double* __restrict__ y,
                                                    const PcgScalars* sc, int check_done) {
   if (check_done && sc_done(sc)) return;
-  constexpr int kpar = COLOUR >> 2;
-  const int nlev = cm.nlev[kpar];
-  const int64_t total = cls_cnt * nlev;
-  const int nz = g.nz;
+  const int64_t total = cls_cnt * cm.nlev[COLOUR >> 2];
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int col = __ldg(cls_cols + cls_off + t / nlev);
-    const int k = 2 * (int)(t % nlev) + kpar;
-    const int64_t row = (int64_t)col * nz + k;
-    const int64_t pi = cm.cbase[COLOUR] + t;
-    double acc = FWD ? r[row] : y[row];
-#pragma unroll
-    for (int s = 0; s < NSLOT; ++s) {
-      if (s == DIAG_SLOT) continue;
-      constexpr int dummy = 0;
-      (void)dummy;
-      const int cj = COLOUR ^ slot_flip(s);
-      if (FWD ? (cj > COLOUR) : (cj < COLOUR)) continue;
-      const int q = slot_q(s);
-      const int kk = k + slot_dk(s);
-      if (kk < 0 || kk >= nz) continue;
-      const int nb = q == 0 ? col : __ldg(g.nbr + (int64_t)col * NNBR + q);
-      if (nb < 0) continue;
-      acc = fma(-F[(int64_t)s * g.n + pi], y[(int64_t)nb * nz + kk], acc);
-    }
-    y[row] = acc * F[(int64_t)DIAG_SLOT * g.n + pi];
-  }
+       t += (int64_t)gridDim.x * blockDim.x)
+    ic0_row<COLOUR, FWD>(g, cm, cls_cols, cls_off, t, F, r, y);
 }
 
 // Grid of the reduction kernels: at most MAX_GRID blocks (the size of the partials buffer).
@@ -1012,6 +1019,8 @@ int ensure_ctx(pm_operator* op) {
   e = e ? e : cudaMalloc((void**)&c->partials, (size_t)NPART * MAX_GRID * sizeof(double));
   e = e ? e : cudaMalloc((void**)&c->sc, sizeof(PcgScalars));
   e = e ? e : cudaMallocHost((void**)&c->sc_host, sizeof(PcgScalars));
+  e = e ? e : cudaMalloc(&c->small_out, 64);
+  e = e ? e : cudaMallocHost(&c->small_out_host, 64);
   if (e == cudaSuccess) e = cudaMemset(c->sc, 0, sizeof(PcgScalars));
   op->ctx = c;
   if (e != cudaSuccess) return cuda_check(e, "solve workspace");
@@ -1277,6 +1286,335 @@ int pcg_run(pm_operator* op, int which, const double* b, double* x, const pm_sol
     return set_error(status, status == PM_NOT_CONVERGED ? "PCG did not reach rtol within max_iter"
                                                         : "PCG breakdown: (p, Ap) <= 0 or non-finite");
   }
+  return PM_OK;
+}
+
+// ---- resident solve of a small system: one block runs the whole PCG ----------------------------
+// The multi-kernel solve costs about twenty launches per IC0 iteration; on a few thousand rows each
+// of them is a few microseconds of launch latency around far less work. Here one block of
+// SMALL_TPB threads runs every step of the same PCG (the same preconditioners, projection,
+// stopping rule and true-residual restarts) with __syncthreads between phases, and writes its
+// statistics to device memory once. The FP64 work of one SM bounds it; it is used where that
+// is cheaper than the launches (n <= SMALL_AUTO_ROWS by default).
+constexpr int SMALL_TPB = 1024;
+constexpr int64_t SMALL_AUTO_ROWS = 16384;   // automatic choice of the resident solve
+constexpr int64_t SMALL_MAX_ROWS = 1 << 20;  // accepted when requested explicitly
+
+struct SmallArgs {
+  double rtol, one_m;
+  int32_t max_iter, max_restarts, x0_is_guess, proj;
+  const double* dinv;     // Jacobi inverse diagonal (ones for PM_PREC_NONE)
+  const uint16_t* keep;   // keep mask of the velocity component (MASKC >= 0)
+  const double* m;        // M 1
+  const double* Fic;      // IC0 factor (colour-ordered rows)
+  const double* Fl;       // line factors (level-major)
+  const int32_t* cls_cols;
+  CMap cm;
+  int64_t cls_off[4], cls_cnt[4];
+};
+
+struct SmallOut {
+  int32_t iters, restarts, first_pass, status, zero_rhs, pad;
+  double rel_true, rel_rec, floor;
+};
+
+// Sum of NV values over the block; every thread receives the totals. red: NV * 32 doubles.
+template <int NV>
+__device__ __forceinline__ void small_sum(double (&v)[NV], double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double t = warp_sum(v[i]);
+    if (lane == 0) red[i * 32 + wid] = t;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double t = 0.0;
+    for (int wv = 0; wv < nw; ++wv) t += red[i * 32 + wv];   // block order: deterministic
+    v[i] = t;
+  }
+  __syncthreads();
+}
+
+template <int MASKC>
+__device__ __forceinline__ double small_row(const Geom& g, const double* __restrict__ val, const double* x,
+                                            const uint16_t* __restrict__ keep, int row) {
+  const int col = row / g.nz, k = row - col * g.nz;
+  bool d = false;
+  return MASKC >= 0 ? row_dot_keep(g, val, x, keep, row, col, k) : row_dot<MASKC>(g, val, x, row, col, k, d);
+}
+
+// z = P^{-1} r for the whole system; leaves (r, z), m'z and 1'r in v (block totals).
+template <int PREC>
+__device__ __forceinline__ void small_precond(const Geom& g, const SmallArgs& a, const double* r, double* z,
+                                              double (&v)[3], double* red) {
+  const int n = (int)g.n, T = blockDim.x, tid = threadIdx.x;
+  if (PREC == PM_PREC_IC0) {
+#define PM_SMALL_PHASE(C, FW)                                                                            \
+  {                                                                                                      \
+    const int64_t tot = a.cls_cnt[(C) & 3] * a.cm.nlev[(C) >> 2];                                        \
+    for (int64_t t = tid; t < tot; t += T) ic0_row<C, FW>(g, a.cm, a.cls_cols, a.cls_off[(C) & 3], t, a.Fic, r, z); \
+    __syncthreads();                                                                                     \
+  }
+    PM_SMALL_PHASE(0, 1) PM_SMALL_PHASE(1, 1) PM_SMALL_PHASE(2, 1) PM_SMALL_PHASE(3, 1)
+    PM_SMALL_PHASE(4, 1) PM_SMALL_PHASE(5, 1) PM_SMALL_PHASE(6, 1) PM_SMALL_PHASE(7, 1)
+    PM_SMALL_PHASE(7, 0) PM_SMALL_PHASE(6, 0) PM_SMALL_PHASE(5, 0) PM_SMALL_PHASE(4, 0)
+    PM_SMALL_PHASE(3, 0) PM_SMALL_PHASE(2, 0) PM_SMALL_PHASE(1, 0) PM_SMALL_PHASE(0, 0)
+#undef PM_SMALL_PHASE
+  } else if (PREC == PM_PREC_LINE) {
+    const int nz = g.nz, ncols = g.ncols;
+    for (int col = tid; col < ncols; col += T) {
+      double y = 0.0;
+      for (int k = 0; k < nz; ++k) {
+        const int li = k * ncols + col;
+        y = (r[col * nz + k] - a.Fl[li] * y) * a.Fl[n + li];
+        z[col * nz + k] = y;
+      }
+      double zn = y;
+      for (int k = nz - 2; k >= 0; --k) {
+        const int li = k * ncols + col;
+        zn = fma(-a.Fl[2 * n + li], zn, z[col * nz + k]);
+        z[col * nz + k] = zn;
+      }
+    }
+    __syncthreads();
+  } else {
+    for (int i = tid; i < n; i += T) z[i] = PREC == PM_PREC_NONE ? r[i] : a.dinv[i] * r[i];
+    __syncthreads();
+  }
+  v[0] = v[1] = v[2] = 0.0;
+  for (int i = tid; i < n; i += T) {
+    const double zi = z[i], ri = r[i];
+    v[0] = fma(ri, zi, v[0]);
+    if (a.proj) {
+      v[1] = fma(a.m[i], zi, v[1]);
+      v[2] += ri;
+    }
+  }
+  small_sum<3>(v, red);
+}
+
+template <int MASKC, int PREC>
+__global__ void __launch_bounds__(SMALL_TPB, 1) k_small_pcg(Geom g, const double* __restrict__ val,
+                                                           const double* __restrict__ b, double* x, double* r,
+                                                           double* p, double* w, double* z, double* bw,
+                                                           SmallArgs a, SmallOut* out) {
+  __shared__ double red[3 * 32];
+  const int n = (int)g.n, T = blockDim.x, tid = threadIdx.x;
+  // right-hand side and initial guess (pressure: b - (1'b / 1'm) m, x shifted to m'x = 0)
+  double v[3] = {0.0, 0.0, 0.0};
+  if (a.proj) {
+    for (int i = tid; i < n; i += T) {
+      v[0] += b[i];
+      if (a.x0_is_guess) v[1] = fma(a.m[i], x[i], v[1]);
+    }
+    small_sum<3>(v, red);
+  }
+  const double lam = a.proj ? v[0] / a.one_m : 0.0, xs = a.proj && a.x0_is_guess ? v[1] / a.one_m : 0.0;
+  const double* bb_ = b;
+  for (int i = tid; i < n; i += T) {
+    if (a.proj) bw[i] = b[i] - lam * a.m[i];
+    x[i] = a.x0_is_guess ? x[i] - xs : 0.0;
+  }
+  if (a.proj) bb_ = bw;
+  __syncthreads();
+  // r = b - A x (compensated), ||b||^2, ||r||^2
+  v[0] = v[1] = v[2] = 0.0;
+  for (int i = tid; i < n; i += T) {
+    const int col = i / g.nz, k = i - col * g.nz;
+    double asum;
+    const double bi = bb_[i];
+    const double ri = row_residual_dot2<MASKC>(g, val, x, bi, i, col, k, asum);
+    r[i] = ri;
+    v[0] = fma(bi, bi, v[0]);
+    v[1] = fma(ri, ri, v[1]);
+  }
+  small_sum<3>(v, red);
+  const double bb = v[0], tol2 = a.rtol * a.rtol * bb;
+  double rr = v[1];
+  int iter = 0, restarts = 0, first_pass = -1, status = PM_OK;
+  double rel_true = 0.0, floor = 0.0, prev_true = -1.0;
+  bool accepted = false;
+  // as pcg_run: x0 may already meet rtol (no iteration), max_iter = 0 allows none
+  bool skip = rr <= tol2;
+  if (!skip && a.max_iter == 0) status = PM_NOT_CONVERGED;
+  if (bb == 0.0) {
+    for (int i = tid; i < n; i += T) x[i] = 0.0;
+  }
+  while (bb != 0.0) {
+    if (status == PM_OK && !skip) {
+      // z = P^{-1} r, rho = (r, z'), p = z' (z' = z - c 1, c = m'z / 1'm for the pressure)
+      small_precond<PREC>(g, a, r, z, v, red);
+      double c = a.proj ? v[1] / a.one_m : 0.0;
+      double rho = v[0] - c * v[2];
+      if (!(rho > 0.0) || !isfinite(rho)) status = PM_BREAKDOWN;
+      for (int i = tid; i < n; i += T) p[i] = z[i] - c;
+      __syncthreads();
+      bool converged = false;
+      while (status == PM_OK && iter < a.max_iter) {
+        // w = A p, (p, w)
+        double pw[1] = {0.0};
+        for (int i = tid; i < n; i += T) {
+          const double wi = small_row<MASKC>(g, val, p, a.keep, i);
+          w[i] = wi;
+          pw[0] = fma(p[i], wi, pw[0]);
+        }
+        small_sum<1>(pw, red);
+        if (!(pw[0] > 0.0) || !isfinite(pw[0])) {
+          status = PM_BREAKDOWN;
+          break;
+        }
+        const double alpha = rho / pw[0];
+        double rv[1] = {0.0};
+        for (int i = tid; i < n; i += T) {
+          x[i] = fma(alpha, p[i], x[i]);
+          const double ri = fma(-alpha, w[i], r[i]);
+          r[i] = ri;
+          rv[0] = fma(ri, ri, rv[0]);
+        }
+        small_sum<1>(rv, red);
+        rr = rv[0];
+        ++iter;
+        if (rr <= tol2) {
+          converged = true;
+          break;
+        }
+        if (iter >= a.max_iter) break;
+        small_precond<PREC>(g, a, r, z, v, red);
+        c = a.proj ? v[1] / a.one_m : 0.0;
+        const double rho_new = v[0] - c * v[2];
+        if (!(rho_new > 0.0) || !isfinite(rho_new)) {
+          status = PM_BREAKDOWN;
+          break;
+        }
+        const double beta = rho_new / rho;
+        rho = rho_new;
+        for (int i = tid; i < n; i += T) p[i] = fma(beta, p[i], z[i] - c);
+        __syncthreads();
+      }
+      if (status == PM_OK && !converged) status = PM_NOT_CONVERGED;   // iteration cap
+    }
+    skip = false;
+    if (first_pass < 0) first_pass = iter;
+    // true residual, compensated (into r, the restart's starting residual), and the acceptance
+    // rule of pcg_run
+    v[0] = v[1] = v[2] = 0.0;
+    for (int i = tid; i < n; i += T) {
+      const int col = i / g.nz, k = i - col * g.nz;
+      double asum;
+      const double bi = bb_[i];
+      const double ri = row_residual_dot2<MASKC>(g, val, x, bi, i, col, k, asum);
+      r[i] = ri;
+      v[0] = fma(ri, ri, v[0]);
+      const double f = asum + fabs(bi);
+      v[1] = fma(f, f, v[1]);
+    }
+    small_sum<3>(v, red);
+    rel_true = sqrt(v[0] / bb);
+    floor = ldexp(1.0, -53) * sqrt(v[1] / bb);
+    const bool stalled = prev_true >= 0.0 && rel_true > 0.5 * prev_true;
+    const bool last = restarts >= a.max_restarts || iter >= a.max_iter;
+    accepted = rel_true <= a.rtol || (rel_true <= floor && (stalled || last));
+    if (status != PM_OK || accepted || last) break;
+    prev_true = rel_true;
+    ++restarts;
+  }
+  if (bb != 0.0 && status == PM_OK && !accepted) status = PM_NOT_CONVERGED;
+  if (a.proj) {   // the returned pressure has m'x = 0
+    __syncthreads();
+    v[0] = v[1] = v[2] = 0.0;
+    for (int i = tid; i < n; i += T) v[0] = fma(a.m[i], x[i], v[0]);
+    small_sum<3>(v, red);
+    const double sh = v[0] / a.one_m;
+    for (int i = tid; i < n; i += T) x[i] -= sh;
+  }
+  if (tid == 0) {
+    out->iters = iter;
+    out->restarts = restarts;
+    out->first_pass = first_pass < 0 ? iter : first_pass;
+    out->status = status;
+    out->zero_rhs = bb == 0.0;
+    out->rel_true = bb == 0.0 ? 0.0 : rel_true;
+    out->rel_rec = bb == 0.0 ? 0.0 : sqrt(rr / bb);
+    out->floor = floor;
+  }
+}
+
+static_assert(sizeof(SmallOut) <= 64, "SmallOut buffer");
+
+template <int MASKC>
+int small_run(pm_operator* op, int which, const double* b, double* x, const pm_solve_opts* o,
+              pm_solve_stats* stats, cudaStream_t s) {
+  auto t0 = std::chrono::steady_clock::now();
+  SolveCtx* c = op->ctx;
+  const bool proj = which == PM_OP_PRESSURE;
+  const int prec = o->prec;
+  int st;
+  if ((st = launch_dinv(op, which, s))) return st;
+  if (prec == PM_PREC_IC0 && !op->ic0[which].ok) {
+    int bd = 0;
+    for (int m = -1; m <= 10; ++m) {
+      if ((st = launch_ic0_factor(op, which, m < 0 ? 0.0 : 1e-3 * std::pow(2.0, m), &bd, s))) return st;
+      if (!bd) break;
+    }
+    if (bd) return set_error(PM_BREAKDOWN, "IC0 pivot failure after the shift limit");
+  }
+  if (prec == PM_PREC_LINE && (st = line_factor(op, which, s))) return st;
+  SmallArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.rtol = o->rtol;
+  a.one_m = op->one_m;
+  a.max_iter = o->max_iter;
+  a.max_restarts = o->max_restarts;
+  a.x0_is_guess = o->x0_is_guess ? 1 : 0;
+  a.proj = proj ? 1 : 0;
+  a.dinv = op->d_dinv[which];
+  a.keep = MASKC >= 0 ? op->d_keep[MASKC < 0 ? 0 : MASKC] : nullptr;
+  a.m = op->d_m;
+  a.Fic = op->ic0[which].F;
+  a.Fl = op->d_line[which];
+  a.cls_cols = op->d_cls_cols;
+  a.cm = cmap_of(op);
+  int64_t off = 0;
+  for (int q = 0; q < 4; ++q) {
+    a.cls_off[q] = off;
+    a.cls_cnt[q] = op->cls_count[q];
+    off += op->cls_count[q];
+  }
+  Geom g = geom_of(op);
+  const double* val = op->d_val[which_valset(which)];
+  SmallOut* dout = static_cast<SmallOut*>(c->small_out);
+#define PM_SMALL(P) k_small_pcg<MASKC, P><<<1, SMALL_TPB, 0, s>>>(g, val, b, x, c->r, c->p, c->w, c->z, c->bw, a, dout)
+  switch (prec) {
+    case PM_PREC_IC0: PM_SMALL(PM_PREC_IC0); break;
+    case PM_PREC_LINE: PM_SMALL(PM_PREC_LINE); break;
+    case PM_PREC_NONE: PM_SMALL(PM_PREC_NONE); break;
+    default: PM_SMALL(PM_PREC_JACOBI); break;
+  }
+#undef PM_SMALL
+  count_launch();
+  if ((st = cuda_check(cudaGetLastError(), "k_small_pcg"))) return st;
+  if ((st = cuda_check(cudaMemcpyAsync(c->small_out_host, c->small_out, sizeof(SmallOut), cudaMemcpyDeviceToHost, s),
+                       "small stats")))
+    return st;
+  if ((st = cuda_check(cudaStreamSynchronize(s), "small pcg"))) return st;
+  const SmallOut& h = *static_cast<const SmallOut*>(c->small_out_host);
+  if (stats) {
+    stats->iters = h.iters;
+    stats->outer_iters = h.restarts;
+    stats->first_pass_iters = h.first_pass;
+    stats->status = h.status;
+    stats->rel_residual_true = h.rel_true;
+    stats->rel_residual_rec = h.rel_rec;
+    stats->rel_residual_floor = h.floor;
+    stats->bytes_moved = h.iters * bytes_per_iter(op, prec, proj);
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (h.status != PM_OK)
+    return set_error(h.status, h.status == PM_NOT_CONVERGED ? "PCG did not reach rtol within max_iter"
+                                                            : "PCG breakdown: (p, Ap) <= 0 or non-finite");
   return PM_OK;
 }
 
@@ -2332,6 +2670,7 @@ int pcg_solve(pm_operator* op, int which, const double* b, double* x, const pm_s
   if (o->prec < 0 || o->prec > PM_PREC_LINE) return set_error(PM_EINVAL, "unknown preconditioner");
   if (!(o->rtol > 0.0) || o->max_iter < 0) return set_error(PM_EINVAL, "rtol must be > 0, max_iter >= 0");
   if (o->precision < PM_FP64 || o->precision > PM_BF16_REFINE) return set_error(PM_EINVAL, "unknown precision");
+  if (o->kernel < PM_KERNEL_AUTO || o->kernel > PM_KERNEL_RESIDENT) return set_error(PM_EINVAL, "unknown kernel choice");
   int r = ensure_ctx(op);
   if (r) return r;
   if (o->precision == PM_FP32_REFINE) {
@@ -2348,6 +2687,17 @@ int pcg_solve(pm_operator* op, int which, const double* b, double* x, const pm_s
       case 1: return mixed_run<1, __nv_bfloat16>(op, which, b, x, o, st, s);
       case 2: return mixed_run<2, __nv_bfloat16>(op, which, b, x, o, st, s);
       default: return mixed_run<-1, __nv_bfloat16>(op, which, b, x, o, st, s);
+    }
+  }
+  const bool resident = o->kernel == PM_KERNEL_RESIDENT || (o->kernel == PM_KERNEL_AUTO && op->n <= SMALL_AUTO_ROWS);
+  if (resident) {
+    if (op->n > SMALL_MAX_ROWS)
+      return set_error(PM_EINVAL, "PM_KERNEL_RESIDENT: at most " + std::to_string(SMALL_MAX_ROWS) + " rows");
+    switch (which_mask(which)) {
+      case 0: return small_run<0>(op, which, b, x, o, st, s);
+      case 1: return small_run<1>(op, which, b, x, o, st, s);
+      case 2: return small_run<2>(op, which, b, x, o, st, s);
+      default: return small_run<-1>(op, which, b, x, o, st, s);
     }
   }
   switch (which_mask(which)) {
@@ -2417,6 +2767,8 @@ void destroy_ctx(pm_operator* op) {
   cudaFree(c->d32);
   cudaFree(c->sc_in);
   if (c->sc_in_host) cudaFreeHost(c->sc_in_host);
+  cudaFree(c->small_out);
+  if (c->small_out_host) cudaFreeHost(c->small_out_host);
   delete c;
   op->ctx = nullptr;
 }

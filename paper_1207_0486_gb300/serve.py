@@ -366,48 +366,3 @@ class GpuBackend:
         if self.server is not None:
             self.server.close()
             self.server = None
-
-
-def resident_load(systems: int = 9, nh: int = 100, nz: int = 30, which: int = 3, quanta: int = 3,
-                  quantum: int = 8, precision: str = "fp32", tile_cols: int = 64, block: int = 128):
-    """Keep `systems` copies of one box basin's system resident in a server and run `quanta`
-    launches of `quantum` iterations (tolerance below reach, so every system stays active).
-    Returns microseconds per iteration of the last launches. A fixed load for timing and profiling
-    the resident kernel."""
-    import torch
-
-    from . import api
-    from workloads import box_basin, random_vector
-    op = api.assemble_operator(box_basin(nh=nh, nz=nz))
-    prc = api.FP32_REFINE if precision == "fp32" else api.FP64
-    srv = api.Server(slots=max(systems, 1), nz_cap=max(nz, 2),
-                     opts=api.Options(rtol=1e-300, prec=api.PREC_LINE, precision=prc, max_iter=10 ** 8,
-                                      inner_rtol=1e-2), tile_cols=tile_cols, block=block)
-    b = torch.from_numpy(random_vector(op.n, 1207)).cuda()
-    xs = [torch.zeros(op.n, dtype=torch.float64, device="cuda") for _ in range(systems)]
-    ws = [torch.empty(srv.workspace_bytes(op), dtype=torch.uint8, device="cuda") for _ in range(systems)]
-    for k in range(systems):
-        srv.admit(op, which, b, xs[k], ws[k])
-    srv.run(1)
-    t0 = time.perf_counter()
-    active = [srv.run(quantum) for _ in range(quanta)]
-    us = (time.perf_counter() - t0) / (quanta * quantum) * 1e6
-    srv.close()
-    op.close()
-    return us, min(active)
-
-
-if __name__ == "__main__":
-    import argparse
-    ap = argparse.ArgumentParser(description="Resident-server load: K systems of one box basin")
-    ap.add_argument("--systems", type=int, default=9)
-    ap.add_argument("--nh", type=int, default=100)
-    ap.add_argument("--nz", type=int, default=30)
-    ap.add_argument("--which", type=int, default=3, help="0-2 velocity component, 3 pressure")
-    ap.add_argument("--quanta", type=int, default=3)
-    ap.add_argument("--quantum", type=int, default=8)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    a = ap.parse_args()
-    us, act = resident_load(a.systems, a.nh, a.nz, a.which, a.quanta, a.quantum, a.precision)
-    print(f"{a.systems} systems, {a.nh}x{a.nh}x{a.nz}, which {a.which}, {a.precision}: {us:.1f} us/iteration "
-          f"(active {act})")

@@ -163,14 +163,23 @@ def test_line_solves_on_32_level_columns(which):
     _check_solve("ocean32", which, pm.PREC_LINE)
 
 
-def _check_solve(name, which, prec):
+@pytest.mark.parametrize("name,kernel", [("box16", pm.KERNEL_STREAM), ("small", pm.KERNEL_STREAM),
+                                         ("ocean48", pm.KERNEL_RESIDENT)])
+@pytest.mark.parametrize("which,prec", SOLVE_CASES)
+def test_pcg_on_the_other_kernel_path(name, kernel, which, prec):
+    """The automatic choice runs box16 and small (2,048 and 325 rows) as one resident block and
+    ocean48 (17,280 rows) as a stream of kernels; here each takes the other path."""
+    _check_solve(name, which, prec, kernel)
+
+
+def _check_solve(name, which, prec, kernel=pm.KERNEL_AUTO):
     b, op, ops = case(name)
     rhs = _rhs(ops, which, 17 + which)
     bd = dev(rhs)
     rtol, tight, soltol = _tolerances(name, which)
     # iteration counts at a working tolerance
     x = torch.zeros_like(bd)
-    st = op.solve(which, bd, x, pm.Options(rtol=rtol, prec=prec))
+    st = op.solve(which, bd, x, pm.Options(rtol=rtol, prec=prec, kernel=kernel))
     ref = _oracle_solve(ops, which, rhs, rtol, prec)
     assert st.status == pm.PM_OK
     # the PCG recurrences: iterations until the recursive residual first meets rtol
@@ -187,7 +196,8 @@ def _check_solve(name, which, prec):
     assert np.linalg.norm(bproj - A @ xg) <= 1.05 * max(rtol, st.rel_residual_floor) * np.linalg.norm(bproj)
     # solution at a tight tolerance against the oracle's
     x = torch.zeros_like(bd)
-    st = op.solve(which, bd, x, pm.Options(rtol=tight, prec=prec, max_restarts=5), allow_not_converged=True)
+    st = op.solve(which, bd, x, pm.Options(rtol=tight, prec=prec, max_restarts=5, kernel=kernel),
+                  allow_not_converged=True)
     ref = _oracle_solve(ops, which, rhs, tight, prec)
     xg = x.cpu().numpy()
     err = np.linalg.norm(xg - ref.x) / np.linalg.norm(ref.x)
