@@ -1296,7 +1296,7 @@ int pcg_run(pm_operator* op, int which, const double* b, double* x, const pm_sol
 // stopping rule and true-residual restarts) with __syncthreads between phases, and writes its
 // statistics to device memory once. The FP64 work of one SM bounds it; it is used where that
 // is cheaper than the launches (n <= SMALL_AUTO_ROWS by default).
-constexpr int SMALL_TPB = 1024;
+constexpr int SMALL_TPB = 256;
 constexpr int64_t SMALL_AUTO_ROWS = 16384;   // automatic choice of the resident solve
 constexpr int64_t SMALL_MAX_ROWS = 1 << 20;  // accepted when requested explicitly
 
@@ -1318,7 +1318,10 @@ struct SmallOut {
   double rel_true, rel_rec, floor;
 };
 
-// Sum of NV values over the block; every thread receives the totals. red: NV * 32 doubles.
+// Sum of NV values over the block; every thread receives the totals. red: NV * 32 + NV doubles.
+// FP64 adds are what the reduction costs on this GPU (its FP64 pipe runs at 1/64 of FP32): the
+// warps' partials are added by one thread per value, in warp order (deterministic), and the
+// totals are read back from shared memory, rather than every thread adding them again.
 template <int NV>
 __device__ __forceinline__ void small_sum(double (&v)[NV], double* red) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1329,12 +1332,14 @@ __device__ __forceinline__ void small_sum(double (&v)[NV], double* red) {
     if (lane == 0) red[i * 32 + wid] = t;
   }
   __syncthreads();
-#pragma unroll
-  for (int i = 0; i < NV; ++i) {
+  if (threadIdx.x < NV) {
     double t = 0.0;
-    for (int wv = 0; wv < nw; ++wv) t += red[i * 32 + wv];   // block order: deterministic
-    v[i] = t;
+    for (int wv = 0; wv < nw; ++wv) t += red[threadIdx.x * 32 + wv];
+    red[NV * 32 + threadIdx.x] = t;
   }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = red[NV * 32 + i];
   __syncthreads();
 }
 
@@ -1401,7 +1406,7 @@ __global__ void __launch_bounds__(SMALL_TPB, 1) k_small_pcg(Geom g, const double
                                                            const double* __restrict__ b, double* x, double* r,
                                                            double* p, double* w, double* z, double* bw,
                                                            SmallArgs a, SmallOut* out) {
-  __shared__ double red[3 * 32];
+  __shared__ double red[3 * 32 + 3];
   const int n = (int)g.n, T = blockDim.x, tid = threadIdx.x;
   // right-hand side and initial guess (pressure: b - (1'b / 1'm) m, x shifted to m'x = 0)
   double v[3] = {0.0, 0.0, 0.0};

@@ -64,7 +64,9 @@ def test_noalloc_matches_the_allocating_solve_and_the_oracle(ops, name, which, p
         st = op.solve_noalloc(which, rhs, x, opts)
         got = x.cpu().numpy()
         assert st.status == pm.PM_OK
-        assert abs(st.iters - st_ref.iters) <= 2, (call, st.iters, st_ref.iters)
+        # the parity rule for iteration counts: within 2, or 2% of a long solve (the two solves
+        # reduce in different orders, and long CG runs are chaotic in the last bits)
+        assert abs(st.iters - st_ref.iters) <= max(2, 0.02 * max(st.iters, st_ref.iters)), (call, st.iters, st_ref.iters)
         err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         assert err <= 1e-9, (call, err)
     torch.cuda.synchronize()
