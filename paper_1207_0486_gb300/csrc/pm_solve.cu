@@ -1932,8 +1932,7 @@ __global__ void __launch_bounds__(LINE_UCOLS) k32_update_line(Geom g, const floa
                                                             const float* __restrict__ p, const float* __restrict__ w,
                                                             float* __restrict__ z, const float2* __restrict__ m2,
                                                             double* partials, PcgScalars* sc, int mode) {
-  // mode 0: first step (z, rho, beta = 0); 1: a full iteration (d, r update, z, rho, beta);
-  // 2: finish an iteration after a residual replacement (z, rho_new, beta = rho_new / rho)
+  // mode 0: first step (z, rho, beta = 0); 1: a full iteration (d, r update, z, rho, beta)
   extern __shared__ float smf[];
   const int update = mode == 1;
   if (mode != 0 && sc_done(sc)) return;
@@ -2005,14 +2004,6 @@ __global__ void __launch_bounds__(LINE_UCOLS) k32_update_line(Geom g, const floa
         sc->status = PM_BREAKDOWN;
         sc->done = 1;
       }
-    } else if (mode == 2) {
-      sc->proj_c = c;
-      sc->beta = rho_new / sc->rho;
-      sc->rho = rho_new;
-      if (!(rho_new > 0.0) || !isfinite(rho_new)) {
-        sc->status = PM_BREAKDOWN;
-        sc->done = 1;
-      }
     } else {
       sc->iter += 1;
       sc->rr = v[0];
@@ -2037,11 +2028,9 @@ __global__ void __launch_bounds__(LINE_UCOLS) k32_update_line(Geom g, const floa
 }
 
 // FP32 version of k_update_line_w (32-level columns, warp tasks of TC columns, no block
-// barriers); the FP32 correction d takes alpha p (folded into the FP64 x at each residual
-// replacement) and the dots are accumulated term by term in FP64. mode as
-// k32_update_line: 0 first step, 1 a full iteration, 2 finish an iteration after a residual
-// replacement. (r, z) = sum_k t_k y_k from the sweep (symmetric column blocks, see
-// k_update_line_w).
+// barriers); the FP32 correction d takes alpha p (folded into the FP64 x at each refinement) and
+// the dots are accumulated in compensated FP32. mode as k32_update_line: 0 first step, 1 a full
+// iteration. (r, z) = sum_k t_k y_k from the sweep (symmetric column blocks, see k_update_line_w).
 template <int PROJ, int TC>
 __global__ void __launch_bounds__(LINE_WTPB, 4) k32_update_line_w(Geom g, const float* __restrict__ F,
                                                               float* __restrict__ d, float* __restrict__ r,
@@ -2122,14 +2111,6 @@ __global__ void __launch_bounds__(LINE_WTPB, 4) k32_update_line_w(Geom g, const 
       sc->rho = rho_new;
       sc->beta = 0.0;
       if ((!(rho_new > 0.0) || !isfinite(rho_new)) && !sc->done) {
-        sc->status = PM_BREAKDOWN;
-        sc->done = 1;
-      }
-    } else if (mode == 2) {
-      sc->proj_c = c;
-      sc->beta = rho_new / sc->rho;
-      sc->rho = rho_new;
-      if (!(rho_new > 0.0) || !isfinite(rho_new)) {
         sc->status = PM_BREAKDOWN;
         sc->done = 1;
       }
@@ -2397,30 +2378,11 @@ void inner_iter(pm_operator* op, int which, const TV* val32, bool proj, int prec
   }
 }
 
-// z = P^{-1} r32, rho = (r, z'). reset_p (first step): beta = 0, p = z'. Otherwise the step
-// that a residual replacement interrupted is finished: beta = rho_new / rho_old, p = z' + beta p.
-void inner_first(pm_operator* op, int which, bool proj, int prec, const float* dinv32, double* x, bool reset_p,
-                 cudaStream_t s) {
+// z = P^{-1} r32, rho = (r, z'), beta = 0, p = z': the first step of an inner solve.
+void inner_first(pm_operator* op, int which, bool proj, int prec, const float* dinv32, double* x, cudaStream_t s) {
   SolveCtx* c = op->ctx;
   Geom g = geom_of(op);
   const int G = grid_for(op->n, TPB, op->num_sms);
-  if (!reset_p) {
-    if (prec == PM_PREC_LINE) {
-      update_line32(op, which, proj, x, 2, s);
-      k32_pupd<1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, c->p32, c->sc_in, 0);
-    } else if (prec == PM_PREC_IC0) {
-      ic0_apply32(op, which, c->r32, c->z32, c->sc_in, 0, s);
-      if (proj) k32_rho<1, 1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, op->d_m2f, c->partials, c->sc_in, 0);
-      else k32_rho<0, 1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, op->d_m2f, c->partials, c->sc_in, 0);
-      k32_pupd<1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, c->p32, c->sc_in, 0);
-    } else {
-      if (proj) k32_rho<1, 0><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, nullptr, op->d_m2f, c->partials, c->sc_in, 0);
-      else k32_rho<0, 0><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, nullptr, op->d_m2f, c->partials, c->sc_in, 0);
-      k32_pupd<0><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, nullptr, c->p32, c->sc_in, 0);
-    }
-    count_launch(2);
-    return;
-  }
   if (prec == PM_PREC_LINE) {
     update_line32(op, which, proj, x, 0, s);
     k32_pupd<1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, c->p32, c->sc_in, 1);
@@ -2498,10 +2460,10 @@ int mixed_run(pm_operator* op, int which, const double* b, double* x, const pm_s
     status = c->sc_host->status;
     rel_true = std::sqrt(c->sc_host->rr / bb);
   } else {
-    // One CG process with reliable updates: x in FP64; r, p, w, z in FP32; dots, alpha and beta
-    // in FP64. The FP32 recursive residual is replaced by the FP64 true residual b - A x each
-    // time it has dropped by inner_rtol since the last replacement, and whenever it claims
-    // convergence; the search direction is kept, so the Krylov process is never restarted.
+    // Restarted refinement: inner PCG solves with r, p, w, z and the correction d in FP32 (dots
+    // in compensated FP32 reduced in FP64, alpha and beta in FP64). Each time the recursive
+    // residual has dropped by inner_rtol, or claims convergence, d is folded into the FP64 x, the
+    // FP64 true residual b - A x (compensated) is formed, and a new inner solve starts from it.
     const double rr_drop = inner_rtol * inner_rtol;
     PcgScalars in;
     std::memset(&in, 0, sizeof(in));
@@ -2514,7 +2476,7 @@ int mixed_run(pm_operator* op, int which, const double* b, double* x, const pm_s
     k32_from64<<<G, TPB, 0, s>>>(op->n, c->r, c->r32);
     count_launch();
     if ((st = cuda_check(cudaMemsetAsync(c->d32, 0, (size_t)op->n * sizeof(float), s), "d32"))) return st;
-    inner_first(op, which, proj, prec, dinv32, x, true, s);
+    inner_first(op, which, proj, prec, dinv32, x, s);
     if ((st = read_inner(c, s))) return st;
     int64_t issued = 0;
     const int32_t zero = 0;
@@ -2556,7 +2518,7 @@ int mixed_run(pm_operator* op, int which, const double* b, double* x, const pm_s
         status = rel_true <= rel_floor ? PM_OK : PM_NOT_CONVERGED;
         break;
       }
-      // residual replacement: r32 = (float)(b - A x); the interrupted step is finished with it
+      // the next inner solve starts from r32 = (float)(b - A x)
       const double thr = rr_drop * c->sc_host->aux[0];
       if ((st = cuda_check(cudaMemcpyAsync(&c->sc_in->done, &zero, sizeof(zero), cudaMemcpyHostToDevice, s), "scalars")))
         return st;
@@ -2564,11 +2526,7 @@ int mixed_run(pm_operator* op, int which, const double* b, double* x, const pm_s
         return st;
       k32_from64<<<G, TPB, 0, s>>>(op->n, c->r, c->r32);
       count_launch();
-      // Restart from the true residual (iterative refinement with an approximate inner solve).
-      // Continuing the Krylov process across the replacement (reliable update: finish the
-      // interrupted step with the replaced residual) is implemented in inner_first but not used:
-      // on the ocean basins it converged far slower than the same scheme emulated on the CPU.
-      inner_first(op, which, proj, prec, dinv32, x, true, s);
+      inner_first(op, which, proj, prec, dinv32, x, s);
       if ((st = read_inner(c, s))) return st;
     }
     inner_total = c->sc_in_host->iter;
