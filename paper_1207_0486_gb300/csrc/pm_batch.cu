@@ -48,6 +48,7 @@ struct Sys {
   const void* dinv;      // T inverse diagonal (Jacobi)
   const void* lineF;     // T line factors (level-major) or null
   const double* m;       // M 1
+  const float2* m2;      // M 1 split into two floats (FP32 systems' m'z), or null
   const double* b;       // right-hand side (caller's), FP64
   double* bw;            // projected right-hand side (pressure) or == b
   double* x;             // solution, FP64
@@ -145,7 +146,7 @@ __device__ __forceinline__ T ldv(const T* p, int i) { return __ldg(p + i); }
 // loaded before the neighbour indices are used, and the iterate with plain loads: this file is
 // compiled with L2-only default loads, and the iterate is written only in other phases.
 template <typename T, int MASKC>
-__device__ __forceinline__ double row_spmv(const Geom& g, const T* __restrict__ val, const T* x, int row, int col,
+__device__ __forceinline__ T row_spmv(const Geom& g, const T* __restrict__ val, const T* x, int row, int col,
                                            int k) {
   constexpr bool MASK = MASKC >= 0;
   const int nz = g.nz, npad = (int)g.npad;
@@ -162,7 +163,7 @@ __device__ __forceinline__ double row_spmv(const Geom& g, const T* __restrict__ 
     for (int q = 0; q < NNBR; ++q) fl[q] = __ldg(g.colflag + (nb[q] >= 0 ? nb[q] : col));
   }
   const T xi = x[row];
-  if (MASK && is_dirichlet(fl[0], k, nz, MASKC)) return (double)xi;
+  if (MASK && is_dirichlet(fl[0], k, nz, MASKC)) return xi;
   if constexpr (std::is_same<T, double>::value) {
     double sum = 0.0;
 #pragma unroll
@@ -192,7 +193,7 @@ __device__ __forceinline__ double row_spmv(const Geom& g, const T* __restrict__ 
       }
       sum = fmaf(keep ? a[s] : 0.f, x[ok ? nb[q] * nz + kk : row] - xi, sum);
     }
-    return (double)fmaf(a[DIAG_SLOT] - drop, xi, sum);
+    return fmaf(a[DIAG_SLOT] - drop, xi, sum);
   }
 }
 
@@ -205,9 +206,9 @@ __device__ __forceinline__ double spmv_tile(const Sys& S, int row0, int rows, in
   const T* val = (const T*)S.val;
   const Geom g = S.g;
   const int bd = blockDim.x;
-  double acc = 0.0;
+  AccFor<T> acc;   // FP64 for FP64 systems, compensated FP32 for FP32 ones
   for (int i0 = threadIdx.x; i0 < rows; i0 += 2 * bd) {
-    double wv[2];
+    T wv[2];
     T pv[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
@@ -218,12 +219,12 @@ __device__ __forceinline__ double spmv_tile(const Sys& S, int row0, int rows, in
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       if (i0 + u * bd < rows) {
-        w[row0 + i0 + u * bd] = (T)wv[u];
-        acc = fma((double)pv[u], wv[u], acc);
+        w[row0 + i0 + u * bd] = wv[u];
+        acc.add_prod(pv[u], wv[u]);
       }
     }
   }
-  return acc;
+  return acc.value();
 }
 
 // Phase A of a REFINE system's tile: r = b' - A x in FP64, compensated (row_residual_dot2), and
@@ -531,6 +532,7 @@ __global__ void __launch_bounds__(256, PM_BATCH_MINB) k_batch(const Sys* __restr
       const Sys& S = sys[tl.sys];
       const int state = scal[tl.sys].state;
       double v[NP] = {0.0, 0.0, 0.0, 0.0};
+      AccFor<T> acc[NP];   // FP64 for FP64 systems, compensated FP32 for FP32 ones
       if (state == ST_SHIFT) {  // partial of m'x for the zero-mean shift
         const int nz = S.g.nz, row0 = tl.col0 * nz, rows = tl.ncols * nz;
         for (int i = tid; i < rows; i += blockDim.x) v[0] = fma(S.m[row0 + i], S.x[row0 + i], v[0]);
@@ -568,7 +570,7 @@ __global__ void __launch_bounds__(256, PM_BATCH_MINB) k_batch(const Sys* __restr
                 ri = ri - (T)alpha * wv[u];
                 r[row] = ri;
               }
-              v[0] = fma((double)ri, (double)ri, v[0]);
+              acc[0].add_prod(ri, ri);
               if (S.prec == PM_PREC_LINE) smt[(i / nz) * ld + i % nz] = ri;
             }
           }
@@ -582,12 +584,14 @@ __global__ void __launch_bounds__(256, PM_BATCH_MINB) k_batch(const Sys* __restr
         for (int i0 = tid; i0 < rows; i0 += U * bd) {
           T rv[U], dv[U];
           double mv[U];
+          float2 m2v[U];
 #pragma unroll
           for (int u = 0; u < U; ++u) {
             const int row = row0 + min(i0 + u * bd, rows - 1);
             rv[u] = ldcg(r + row);
             dv[u] = line ? (T)0 : __ldg(dinv + row);
-            mv[u] = S.proj ? __ldg(S.m + row) : 0.0;
+            if (std::is_same<T, float>::value) m2v[u] = S.proj ? __ldg(S.m2 + row) : make_float2(0.f, 0.f);
+            else mv[u] = S.proj ? __ldg(S.m + row) : 0.0;
           }
 #pragma unroll
           for (int u = 0; u < U; ++u) {
@@ -596,14 +600,20 @@ __global__ void __launch_bounds__(256, PM_BATCH_MINB) k_batch(const Sys* __restr
               const T ri = rv[u];
               const T zi = line ? smt[(i / nz) * ld + i % nz] : (T)(dv[u] * ri);
               z[row0 + i] = zi;
-              v[1] = fma((double)ri, (double)zi, v[1]);
+              acc[1].add_prod(ri, zi);
               if (S.proj) {
-                v[2] = fma(mv[u], (double)zi, v[2]);
-                v[3] += (double)ri;
+                if constexpr (std::is_same<T, float>::value) {
+                  acc[2].add_prod(m2v[u].x, zi);
+                  acc[2].add_prod(m2v[u].y, zi);
+                } else {
+                  acc[2].add_prod(mv[u], zi);
+                }
+                acc[3].add(ri);
               }
             }
           }
         }
+        for (int l = 0; l < NP; ++l) v[l] = acc[l].value();
       }
       block_sum<NP>(v, red);
       if (tid == 0)
@@ -796,6 +806,8 @@ int build_layout(pm_batch* bt) {
     S.dinv = f32 ? (const void*)op->d_dinv32[w] : (const void*)op->d_dinv[w];
     S.lineF = bt->prec == PM_PREC_LINE ? (f32 ? (const void*)op->d_line32[w] : (const void*)op->d_line[w]) : nullptr;
     S.m = op->d_m;
+  S.m2 = op->d_m2f;
+    S.m2 = op->d_m2f;
     S.one_m = op->one_m;
     S.maskc = which_mask(w);
     S.proj = w == PM_OP_PRESSURE;
@@ -1334,6 +1346,7 @@ extern "C" int pm_server_admit(pm_server* sv, pm_operator* op, pm_which which, c
   S.dinv = f32 ? (const void*)op->d_dinv32[w] : (const void*)op->d_dinv[w];
   S.lineF = sv->prec == PM_PREC_LINE ? (f32 ? (const void*)op->d_line32[w] : (const void*)op->d_line[w]) : nullptr;
   S.m = op->d_m;
+  S.m2 = op->d_m2f;
   S.one_m = op->one_m;
   S.maskc = which_mask(w);
   S.proj = w == PM_OP_PRESSURE;

@@ -96,6 +96,43 @@ __device__ __forceinline__ double two_product(double a, double b, double& err) {
   return p;
 }
 
+// Compensated FP32 ("double-float") accumulation of the mixed-precision dot products. GB300's
+// FP64 pipe runs at 1/64 of its FP32 rate, and an FP64 dot of FP32 vectors costs two conversions
+// and an FP64 FMA per term on that pipe, which made the FP32 kernels FP64-bound. Here each product
+// a b is split exactly into p + e by one FP32 FMA (TwoProduct), p is added to the running sum by
+// TwoSum, and both rounding errors go into a second FP32 word: a thread's partial sum keeps about
+// 48 significant bits (relative error of order n u32^2 for its n terms, u32 = 2^-24) and becomes
+// an FP64 number once, where the FP64 block and grid reductions take over.
+struct DF {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float a) {
+    const float s = __fadd_rn(hi, a);
+    const float bv = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(a, bv));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float pr = __fmul_rn(a, b);
+    const float pe = fmaf(a, b, -pr);
+    add(pr);
+    lo = __fadd_rn(lo, pe);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// The same interface accumulating in FP64 (the FP64 kernels' dots), so that a kernel templated on
+// its vector type can pick its accumulator: AccFor<float> = DF, AccFor<double> = Acc64.
+struct Acc64 {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double a) { v += a; }
+  __device__ __forceinline__ void add_prod(double a, double b) { v = fma(a, b, v); }
+  __device__ __forceinline__ double value() const { return v; }
+};
+template <typename T> struct AccSel { using type = Acc64; };
+template <> struct AccSel<float> { using type = DF; };
+template <typename T> using AccFor = typename AccSel<T>::type;
+
 // Device view of a basin's mesh.
 struct Geom {
   int32_t ncols, nz;

@@ -1629,31 +1629,6 @@ int small_run(pm_operator* op, int which, const double* b, double* x, const pm_s
 // FP32 SpMV / preconditioner arithmetic, FP64 dot products and alpha / beta, to a relative
 // reduction inner_rtol; then x += d in FP64.
 
-// Compensated FP32 ("double-float") accumulation of the mixed-precision dot products. GB300's
-// FP64 pipe runs at 1/64 of its FP32 rate, and an FP64 dot of FP32 vectors costs two conversions
-// and an FP64 FMA per term on that pipe, which made the FP32 kernels FP64-bound. Here each product
-// a b is split exactly into p + e by one FP32 FMA (TwoProduct), p is added to the running sum by
-// TwoSum, and both rounding errors go into a second FP32 word: a thread's partial sum keeps about
-// 48 significant bits (relative error of order n u32^2 for its n terms, u32 = 2^-24) and becomes
-// an FP64 number once, where the FP64 block and grid reductions take over.
-struct DF {
-  float hi = 0.f, lo = 0.f;
-  __device__ __forceinline__ void add(float a) {
-    const float s = __fadd_rn(hi, a);
-    const float bv = __fsub_rn(s, hi);
-    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(a, bv));
-    hi = s;
-    lo = __fadd_rn(lo, e);
-  }
-  __device__ __forceinline__ void add_prod(float a, float b) {
-    const float pr = __fmul_rn(a, b);
-    const float pe = fmaf(a, b, -pr);
-    add(pr);
-    lo = __fadd_rn(lo, pe);
-  }
-  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
-};
-
 // m'z with m held exactly as two floats (hi + lo = m in FP64 to 48 bits) for the FP32 kernels.
 __device__ __forceinline__ void add_mz(DF& acc, float2 m2, float z) {
   acc.add_prod(m2.x, z);
