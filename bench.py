@@ -411,6 +411,7 @@ def run_batched_leg(dist, world, rank):
     nsys = _gather_sum(dist, len(sys_ops))
     nodes = _gather_sum(dist, sum(op.n for op in ops))
     bad = _gather_sum(dist, sum(1 for s in stats if s.status != pm.PM_OK))
+    mass = _consistent_mass_batch(dist, ops, gen)
     for op in ops:
         op.close()
     return {"workload": "64 seeded basins, sides log-uniform 48-384, 8-48 layers, 4 right-hand sides each",
@@ -420,7 +421,51 @@ def run_batched_leg(dist, world, rank):
             "solves_per_s": round(nsys / t_batch, 2), "sequential_solves_per_s": round(nsys / t_seq, 2),
             "speedup_vs_sequential_fp64": round(t_seq / t_batch, 3), "failed": int(bad),
             "iters_max": max(int(s.iters) for s in stats), "sequential_iters_max": max(int(s.iters) for s in sst),
-            "autotuned": info}
+            "autotuned": info, "consistent_mass_ic0": mass}
+
+
+def _consistent_mass_batch(dist, ops, gen):
+    """The consistent-mass velocity correction of every basin (M u = rhs for the three components,
+    IC0-PCG to 1e-10) in one batched launch, FP64 and FP32-with-refinement, against the same solves
+    one after another on the single-system FP64 path."""
+    import torch
+    import paper_1207_0486_gb300 as pm
+
+    sys_ops = [op for op in ops for _ in range(3)]
+    bs = [torch.randn(op.n, dtype=torch.float64, device="cuda", generator=gen) for op in sys_ops]
+    xs = [torch.zeros_like(b) for b in bs]
+    sys_w = [pm.OP_MASS] * len(sys_ops)
+    out = {"systems": int(_gather_sum(dist, len(sys_ops))), "preconditioner": "multicolour IC0", "rtol": 1e-10}
+    for label, precision in (("fp64", pm.FP64), ("fp32_refine", pm.FP32_REFINE)):
+        batch = pm.Batch(sys_ops, sys_w, pm.Options(rtol=1e-10, prec=pm.PREC_IC0, precision=precision,
+                                                    inner_rtol=1e-4, max_iter=10000))
+        batch.solve(bs, xs, allow_not_converged=True)  # warm-up (graph capture)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        stats = batch.solve(bs, xs, allow_not_converged=True)
+        torch.cuda.synchronize()
+        t = _gather_max(dist, time.perf_counter() - t0)
+        batch.close()
+        out[label] = {"batched_s": round(t, 4), "solves_per_s": round(out["systems"] / t, 1),
+                      "failed": int(_gather_sum(dist, sum(1 for st in stats if st.status != pm.PM_OK))),
+                      "iters_max": max(int(st.iters) for st in stats)}
+    seq = pm.Options(rtol=1e-10, prec=pm.PREC_IC0, precision=pm.FP64, max_iter=10000, max_restarts=5)
+    for op, b, x in zip(sys_ops[:1], bs[:1], xs[:1]):  # factors built outside the timed region
+        op.solve(pm.OP_MASS, b, x, seq, allow_not_converged=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sst = [op.solve(pm.OP_MASS, b, x, seq, allow_not_converged=True) for op, b, x in zip(sys_ops, bs, xs)]
+    torch.cuda.synchronize()
+    t_seq = _gather_max(dist, time.perf_counter() - t0)
+    out["sequential_fp64_s"] = round(t_seq, 4)
+    out["sequential_iters_max"] = max(int(st.iters) for st in sst)
+    for label in ("fp64", "fp32_refine"):
+        out[label]["speedup_vs_sequential_fp64"] = round(t_seq / out[label]["batched_s"], 3)
+    return out
 
 
 def run_serving_leg(dist, world, rank, n_requests):

@@ -53,6 +53,12 @@ struct Sys {
   double* bw;            // projected right-hand side (pressure) or == b
   double* x;             // solution, FP64
   void *r, *p, *w, *z;   // Krylov vectors (T)
+  const void* ic0F;      // T IC0 factor (colour-ordered rows, 1 / L_ii on the diagonal) or null
+  const int32_t* clsidx; // per column: index within its parity class (IC0 row positions)
+  const int32_t* coli;   // per column: grid indices (parity class)
+  const int32_t* colj;
+  int64_t cbase[8];      // first colour-ordered position of each colour
+  int32_t nlev[2];       // levels of even / odd parity
   double one_m;
   int32_t maskc, proj, prec, tile0, ntiles, pad;
 };
@@ -303,6 +309,46 @@ __device__ __forceinline__ void line_sweep(T* cs, const T* __restrict__ F, int c
   }
 }
 
+// One row of an IC0 colour phase (runtime colour; the same update as the single-system sweeps):
+// forward y_i = (r_i - sum_{colour(j) < c} L_ij y_j) / L_ii, backward z_i = (y_i - sum_{colour(j) > c}
+// L_ji z_j) / L_ii in place on y. The diagonal slot of F holds 1 / L_ii.
+template <typename T>
+__device__ __forceinline__ void ic0_row_rt(const Geom& g, int colour, bool fwd, int col, int k, int64_t pi,
+                                           const T* __restrict__ F, const T* r, T* y) {
+  const int nz = g.nz;
+  const int64_t row = (int64_t)col * nz + k;
+  T acc = fwd ? r[row] : y[row];
+#pragma unroll
+  for (int s = 0; s < NSLOT; ++s) {
+    if (s == DIAG_SLOT) continue;
+    const int cj = colour ^ slot_flip(s);
+    if (fwd ? (cj > colour) : (cj < colour)) continue;
+    const int kk = k + slot_dk(s);
+    if (kk < 0 || kk >= nz) continue;
+    const int q = slot_q(s);
+    const int nb = q == 0 ? col : __ldg(g.nbr + (int64_t)col * NNBR + q);
+    if (nb < 0) continue;
+    acc = fma(-__ldg(F + (int64_t)s * g.n + pi), y[(int64_t)nb * nz + kk], acc);
+  }
+  y[row] = acc * __ldg(F + (int64_t)DIAG_SLOT * g.n + pi);
+}
+
+// The rows of one tile in one IC0 colour phase: columns of the colour's parity class, levels of
+// its parity (position = cbase[c] + index of the column in its class * levels + k / 2).
+template <typename T>
+__device__ __forceinline__ void ic0_tile(const Sys& S, const Tile& tl, int colour, bool fwd) {
+  const int kpar = colour >> 2, cls = colour & 3;
+  const int nlev = S.nlev[kpar];
+  const T* F = (const T*)S.ic0F;
+  for (int i = threadIdx.x; i < tl.ncols * nlev; i += blockDim.x) {
+    const int col = tl.col0 + i / nlev;
+    if (((__ldg(S.coli + col) & 1) | ((__ldg(S.colj + col) & 1) << 1)) != cls) continue;
+    const int k = 2 * (i % nlev) + kpar;
+    const int64_t pi = S.cbase[colour] + (int64_t)__ldg(S.clsidx + col) * nlev + (k >> 1);
+    ic0_row_rt<T>(S.g, colour, fwd, col, k, pi, F, (const T*)S.r, (T*)S.z);
+  }
+}
+
 // Ordered list (shared memory) of the systems active in a phase, built by every block from the
 // states in one parallel pass; returns its length. Tiles a block owns in a system: t = blockIdx.x
 // mod gridDim.x within the system's range, so which block runs a tile never changes the sums.
@@ -339,6 +385,19 @@ __device__ __forceinline__ int first_owned(const Sys* sys, int s) {
     for (int t = first_owned(sys, slist[a_]), te_ = sys[slist[a_]].tile0 + sys[slist[a_]].ntiles; \
          t < te_; t += gridDim.x)
 
+// The 16 colour phases of an IC0 apply over the tiles of the systems active in MODE (SHIFT systems
+// skipped), a grid barrier after each: a phase reads the rows the previous phases wrote in other
+// tiles. Leaves the kernel (return) when a barrier times out.
+#define IC0_PHASES(MODE)                                                                            \
+  for (int ph_ = 0; ph_ < 16; ++ph_) {                                                              \
+    const int col_ = ph_ < 8 ? ph_ : 15 - ph_;                                                      \
+    FOR_OWNED_TILES(MODE, t) {                                                                      \
+      if (scal[tiles[t].sys].state == ST_SHIFT) continue;                                           \
+      ic0_tile<T>(sys[tiles[t].sys], tiles[t], col_, ph_ < 8);                                      \
+    }                                                                                               \
+    if (!grid_barrier(ctl)) return;                                                                 \
+  }
+
 // Resident blocks of 256 threads per SM the register budget is sized for (128 registers at 2: no
 // spills; measured faster than 80 registers at 3 for the long pressure solves).
 #ifndef PM_BATCH_MINB
@@ -348,7 +407,7 @@ __device__ __forceinline__ int first_owned(const Sys* sys, int s) {
 template <typename T>
 __global__ void __launch_bounds__(256, PM_BATCH_MINB) k_batch(const Sys* __restrict__ sys, Scal* scal, int nsys,
                                                const Tile* __restrict__ tiles, int ntiles, double* part, Ctl* ctl,
-                                               int quantum, int init) {
+                                               int quantum, int init, int ic0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int* slist = reinterpret_cast<int*>(smem_raw);                             // nsys entries
   T* smt = reinterpret_cast<T*>(smem_raw + ((size_t)nsys * 4 + 15) / 16 * 16);  // tile of columns
@@ -397,6 +456,10 @@ __global__ void __launch_bounds__(256, PM_BATCH_MINB) k_batch(const Sys* __restr
         v[0] = fma(bi, bi, v[0]);
         if (S.prec == PM_PREC_LINE) smt[(i / nz) * ld + i % nz] = (T)bi;
       }
+      if (ic0) {   // z comes from the colour phases below; the partials after them
+        __syncthreads();
+        continue;
+      }
       __syncthreads();
       if (S.prec == PM_PREC_LINE && tid < tl.ncols)
         line_sweep<T>(smt + tid * ld, (const T*)S.lineF, tl.col0 + tid, S.g.ncols, (int)S.g.n, nz);
@@ -418,6 +481,31 @@ __global__ void __launch_bounds__(256, PM_BATCH_MINB) k_batch(const Sys* __restr
       __syncthreads();
     }
     if (!grid_barrier(ctl)) return;
+    if (ic0) {
+      IC0_PHASES(3)
+      FOR_OWNED_TILES(3, t) {   // partials: (b', b'), (r, z), m'z, 1'r
+        const Tile tl = tiles[t];
+        const Sys& S = sys[tl.sys];
+        const int nz = S.g.nz, row0 = tl.col0 * nz, rows = tl.ncols * nz;
+        double v[NP] = {0.0, 0.0, 0.0, 0.0};
+        for (int i = tid; i < rows; i += blockDim.x) {
+          const int row = row0 + i;
+          const double bi = S.bw[row];
+          const T ri = ((const T*)S.r)[row], zi = ((const T*)S.z)[row];
+          v[0] = fma(bi, bi, v[0]);
+          v[1] = fma((double)ri, (double)zi, v[1]);
+          if (S.proj) {
+            v[2] = fma(S.m[row], (double)zi, v[2]);
+            v[3] += (double)ri;
+          }
+        }
+        block_sum<NP>(v, red);
+        if (tid == 0)
+          for (int l = 0; l < NP; ++l) part[(int64_t)l * ntiles + t] = v[l];
+        __syncthreads();
+      }
+      if (!grid_barrier(ctl)) return;
+    }
     for (int s = blockIdx.x; s < nsys; s += gridDim.x) {
       const Sys& S = sys[s];
       if (scal[s].state != ST_NEW) continue;
@@ -576,6 +664,10 @@ __global__ void __launch_bounds__(256, PM_BATCH_MINB) k_batch(const Sys* __restr
           }
         }
         __syncthreads();
+        if (ic0) {   // z from the colour phases after this one, (r, z), m'z, 1'r after them
+          v[0] = acc[0].value();
+          goto b_partials;
+        }
         if (S.prec == PM_PREC_LINE && tid < tl.ncols)
           line_sweep<T>(smt + tid * ld, (const T*)S.lineF, tl.col0 + tid, S.g.ncols, (int)S.g.n, nz);
         __syncthreads();
@@ -615,12 +707,44 @@ __global__ void __launch_bounds__(256, PM_BATCH_MINB) k_batch(const Sys* __restr
         }
         for (int l = 0; l < NP; ++l) v[l] = acc[l].value();
       }
+    b_partials:
       block_sum<NP>(v, red);
       if (tid == 0)
         for (int l = 0; l < NP; ++l) part[(int64_t)l * ntiles + t] = v[l];
       __syncthreads();
     }
     if (!grid_barrier(ctl)) return;
+    if (ic0) {
+      IC0_PHASES(1)
+      FOR_OWNED_TILES(1, t) {   // (r, z), m'z, 1'r of ITER / RESTART tiles into lanes 1..3
+        const Tile tl = tiles[t];
+        const Sys& S = sys[tl.sys];
+        if (scal[tl.sys].state == ST_SHIFT) continue;
+        const int nz = S.g.nz, row0 = tl.col0 * nz, rows = tl.ncols * nz;
+        AccFor<T> acc[NP];
+        for (int i = tid; i < rows; i += blockDim.x) {
+          const int row = row0 + i;
+          const T ri = ldcg((const T*)S.r + row), zi = ldcg((const T*)S.z + row);
+          acc[1].add_prod(ri, zi);
+          if (S.proj) {
+            if constexpr (std::is_same<T, float>::value) {
+              const float2 m2 = __ldg(S.m2 + row);
+              acc[2].add_prod(m2.x, zi);
+              acc[2].add_prod(m2.y, zi);
+            } else {
+              acc[2].add_prod(__ldg(S.m + row), zi);
+            }
+            acc[3].add(ri);
+          }
+        }
+        double v[NP] = {0.0, acc[1].value(), acc[2].value(), acc[3].value()};
+        block_sum<NP>(v, red);
+        if (tid == 0)
+          for (int l = 1; l < NP; ++l) part[(int64_t)l * ntiles + t] = v[l];
+        __syncthreads();
+      }
+      if (!grid_barrier(ctl)) return;
+    }
     // ---- Br ------------------------------------------------------------------------------------------
     for (int s = blockIdx.x; s < nsys; s += gridDim.x) {
       const Sys& S = sys[s];
@@ -759,6 +883,24 @@ size_t kernel_smem(int nsys, int tile_cols, int nz, int precision) {
 
 size_t smem_bytes(const pm_batch* bt) { return kernel_smem(bt->count, bt->tile_cols, bt->nz_max, bt->precision); }
 
+// The IC0 fields of a system descriptor: factor (FP64 or its FP32 copy), column-class index and
+// grid parities (the packed column arrays of the operator), colour bases and level counts.
+void fill_ic0(Sys* S, const pm_operator* op, int which, int prec, bool f32) {
+  S->ic0F = nullptr;
+  if (prec != PM_PREC_IC0) return;
+  S->ic0F = f32 ? (const void*)op->d_ic0_32[which] : (const void*)op->ic0[which].F;
+  S->clsidx = op->d_cls_cols + op->ncols;
+  S->coli = S->clsidx + op->ncols;
+  S->colj = S->coli + op->ncols;
+  S->nlev[0] = (op->nz + 1) / 2;
+  S->nlev[1] = op->nz / 2;
+  int64_t acc = 0;
+  for (int c = 0; c < 8; ++c) {
+    S->cbase[c] = acc;
+    acc += (int64_t)op->cls_count[c & 3] * S->nlev[c >> 2];
+  }
+}
+
 void free_layout(pm_batch* bt) {
   if (bt->graph) cudaGraphExecDestroy(bt->graph);
   bt->graph = nullptr;
@@ -805,6 +947,7 @@ int build_layout(pm_batch* bt) {
     S.val64 = op->d_val[vs];
     S.dinv = f32 ? (const void*)op->d_dinv32[w] : (const void*)op->d_dinv[w];
     S.lineF = bt->prec == PM_PREC_LINE ? (f32 ? (const void*)op->d_line32[w] : (const void*)op->d_line[w]) : nullptr;
+    fill_ic0(&S, op, w, bt->prec, f32);
     S.m = op->d_m;
   S.m2 = op->d_m2f;
     S.m2 = op->d_m2f;
@@ -834,7 +977,7 @@ int build_layout(pm_batch* bt) {
 
 template <typename T>
 cudaError_t launch_k(int grid, int block, size_t smem, const Sys* d_sys, Scal* d_scal, int nsys, const Tile* d_tiles,
-                     int ntiles, double* d_part, Ctl* d_ctl, int quantum, int init, cudaStream_t s) {
+                     int ntiles, double* d_part, Ctl* d_ctl, int quantum, int init, int ic0, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);
@@ -846,13 +989,13 @@ cudaError_t launch_k(int grid, int block, size_t smem, const Sys* d_sys, Scal* d
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   count_launch();
-  return cudaLaunchKernelEx(&cfg, k_batch<T>, d_sys, d_scal, nsys, d_tiles, ntiles, d_part, d_ctl, quantum, init);
+  return cudaLaunchKernelEx(&cfg, k_batch<T>, d_sys, d_scal, nsys, d_tiles, ntiles, d_part, d_ctl, quantum, init, ic0);
 }
 
 template <typename T>
 cudaError_t launch(pm_batch* bt, int quantum, int init, cudaStream_t s) {
   return launch_k<T>(bt->grid, bt->block, smem_bytes(bt), bt->d_sys, bt->d_scal, (int)bt->count, bt->d_tiles,
-                     (int)bt->ntiles, bt->d_part, bt->d_ctl, quantum, init, s);
+                     (int)bt->ntiles, bt->d_part, bt->d_ctl, quantum, init, bt->prec == PM_PREC_IC0 ? 1 : 0, s);
 }
 
 // Capture one launch (made by `fn` on the capture stream) into an executable graph.
@@ -1043,8 +1186,9 @@ extern "C" int pm_batch_create(pm_operator* const* ops, const pm_which* which, i
                                const pm_solve_opts* opts, int32_t autotune, pm_batch** out, pm_stream stream) {
   if (!ops || !which || !opts || !out || count <= 0 || count > 4096) return set_error(PM_EINVAL, "bad batch arguments");
   *out = nullptr;
-  if (opts->prec != PM_PREC_JACOBI && opts->prec != PM_PREC_LINE && opts->prec != PM_PREC_NONE)
-    return set_error(PM_EINVAL, "batched PCG supports PM_PREC_JACOBI, PM_PREC_LINE and PM_PREC_NONE");
+  if (opts->prec != PM_PREC_JACOBI && opts->prec != PM_PREC_LINE && opts->prec != PM_PREC_NONE &&
+      opts->prec != PM_PREC_IC0)
+    return set_error(PM_EINVAL, "unknown preconditioner");
   if (opts->precision != PM_FP64 && opts->precision != PM_FP32_REFINE)
     return set_error(PM_EINVAL, "batched PCG supports PM_FP64 and PM_FP32_REFINE");
   if (!(opts->rtol > 0.0)) return set_error(PM_EINVAL, "rtol must be > 0");
@@ -1240,8 +1384,9 @@ extern "C" int pm_server_create(int32_t slots, int32_t nz_cap, const pm_solve_op
   if (!opts || !out || slots <= 0 || slots > 4096 || nz_cap < 2 || nz_cap > 4096)
     return set_error(PM_EINVAL, "bad server arguments");
   *out = nullptr;
-  if (opts->prec != PM_PREC_JACOBI && opts->prec != PM_PREC_LINE && opts->prec != PM_PREC_NONE)
-    return set_error(PM_EINVAL, "server supports PM_PREC_JACOBI, PM_PREC_LINE and PM_PREC_NONE");
+  if (opts->prec != PM_PREC_JACOBI && opts->prec != PM_PREC_LINE && opts->prec != PM_PREC_NONE &&
+      opts->prec != PM_PREC_IC0)
+    return set_error(PM_EINVAL, "unknown preconditioner");
   if (opts->precision != PM_FP64 && opts->precision != PM_FP32_REFINE)
     return set_error(PM_EINVAL, "server supports PM_FP64 and PM_FP32_REFINE");
   if (!(opts->rtol > 0.0)) return set_error(PM_EINVAL, "rtol must be > 0");
@@ -1345,6 +1490,7 @@ extern "C" int pm_server_admit(pm_server* sv, pm_operator* op, pm_which which, c
   S.val64 = op->d_val[vs];
   S.dinv = f32 ? (const void*)op->d_dinv32[w] : (const void*)op->d_dinv[w];
   S.lineF = sv->prec == PM_PREC_LINE ? (f32 ? (const void*)op->d_line32[w] : (const void*)op->d_line[w]) : nullptr;
+  fill_ic0(&S, op, w, sv->prec, f32);
   S.m = op->d_m;
   S.m2 = op->d_m2f;
   S.one_m = op->one_m;
@@ -1404,9 +1550,9 @@ extern "C" int pm_server_run(pm_server* sv, int32_t quantum, int32_t* active, pm
     st = capture_graph(&sv->graph, [&](cudaStream_t cs) {
       return sv->precision == PM_FP64
                  ? launch_k<double>(sv->grid, sv->block, smem, sv->d_sys, sv->d_scal, sv->cap, sv->d_tiles,
-                                    (int)sv->tcap, sv->d_part, sv->d_ctl, quantum, 0, cs)
+                                    (int)sv->tcap, sv->d_part, sv->d_ctl, quantum, 0, sv->prec == PM_PREC_IC0 ? 1 : 0, cs)
                  : launch_k<float>(sv->grid, sv->block, smem, sv->d_sys, sv->d_scal, sv->cap, sv->d_tiles,
-                                   (int)sv->tcap, sv->d_part, sv->d_ctl, quantum, 0, cs);
+                                   (int)sv->tcap, sv->d_part, sv->d_ctl, quantum, 0, sv->prec == PM_PREC_IC0 ? 1 : 0, cs);
     });
     if (st) return st;
     sv->graph_quantum = quantum;

@@ -2646,13 +2646,21 @@ int pcg_solve(pm_operator* op, int which, const double* b, double* x, const pm_s
   }
 }
 
-// Everything a batched solve reads from one operator: Jacobi diagonals, line factors, and for
-// FP32 the difference-form values and FP32 factors.
+// Everything a batched solve reads from one operator: Jacobi diagonals, line or IC0 factors, and
+// for FP32 the difference-form values and FP32 factors.
 int prepare_for_batch(pm_operator* op, int which, int prec, int precision, cudaStream_t s) {
   int st = ensure_ctx(op);
   if (st) return st;
   if ((st = launch_dinv(op, which, s))) return st;
   if (prec == PM_PREC_LINE && (st = line_factor(op, which, s))) return st;
+  if (prec == PM_PREC_IC0 && !op->ic0[which].ok) {
+    int bd = 0;
+    for (int m = -1; m <= 10; ++m) {
+      if ((st = launch_ic0_factor(op, which, m < 0 ? 0.0 : 1e-3 * std::pow(2.0, m), &bd, s))) return st;
+      if (!bd) break;
+    }
+    if (bd) return set_error(PM_BREAKDOWN, "IC0 pivot failure after the shift limit");
+  }
   if (precision != PM_FP64 && (st = ensure_mixed(op, which, precision, prec, s))) return st;
   return PM_OK;
 }

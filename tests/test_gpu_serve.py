@@ -23,14 +23,15 @@ def oracle_solve(ops, which, rhs):
     return opcg.pcg(A, rhs, rtol=1e-13, precond=opcg.jacobi_preconditioner(A)).x
 
 
-@pytest.mark.parametrize("precision", [pm.FP64, pm.FP32_REFINE])
-def test_staggered_admission_matches_one_shot_batch(precision):
+@pytest.mark.parametrize("precision,prec", [(pm.FP64, pm.PREC_LINE), (pm.FP32_REFINE, pm.PREC_LINE),
+                                            (pm.FP64, pm.PREC_IC0), (pm.FP32_REFINE, pm.PREC_IC0)])
+def test_staggered_admission_matches_one_shot_batch(precision, prec):
     """Same tile width and block as the one-shot batch: admitted in three waves between quanta,
     every system reproduces the batch's bits and iteration counts."""
     rtol = 1e-10 if precision == pm.FP64 else 1e-8
-    ref_x, ref_st, info = run_batch(ENTRIES, pm.PREC_LINE, precision=precision, rtol=rtol)
+    ref_x, ref_st, info = run_batch(ENTRIES, prec, precision=precision, rtol=rtol)
     # the options run_batch uses (its inner_rtol is the Options default)
-    srv = pm.Server(slots=8, nz_cap=16, opts=pm.Options(rtol=rtol, prec=pm.PREC_LINE, precision=precision,
+    srv = pm.Server(slots=8, nz_cap=16, opts=pm.Options(rtol=rtol, prec=prec, precision=precision,
                                                         max_iter=200000),
                     tile_cols=info["tile_cols"], block=info["block"])
     bs, xs, ws, slot_of = [], [], [], {}
