@@ -102,6 +102,8 @@ typedef enum pm_which {
  * pressure system of a thin layered domain (the paper's "DIAG + LS CGS OPT" is not defined in
  * it), not the paper's method. */
 enum { PM_PREC_JACOBI = 0, PM_PREC_IC0 = 1, PM_PREC_NONE = 2, PM_PREC_LINE = 3 };
+/* In per-entry preconditioner arguments (batches, server admission): use the options' choice. */
+#define PM_PREC_DEFAULT (-1)
 /* Arithmetic of the inner iteration. FP64 throughout, or FP32 (BF16) operator values with FP32
  * vectors inside PCG, FP64 dot products / alpha / beta, and FP64 outer iterative refinement on
  * the true residual until rtol is met. */
@@ -221,16 +223,21 @@ int pm_pcg_solve_noalloc(pm_operator* op, pm_which which, const double* b, doubl
 /* A batch of independent systems (operator ops[i] with which[i]), solved together by one
  * persistent cooperative kernel per quantum of iterations, captured once in a CUDA graph and
  * replayed: PCG of the Section 5 remark for every system, all systems advancing together, each
- * with its own alpha / beta / convergence. Supported: PM_PREC_JACOBI, PM_PREC_LINE, PM_PREC_IC0
- * (PM_PREC_NONE maps to Jacobi); PM_FP64, or PM_FP32_REFINE (FP32 difference-form values and
- * vectors, FP64 x, dots and true-residual restarts). IC0 applies the same multicolour factor as
- * the single-system solve: its 16 colour sweeps run as 16 phases of the persistent kernel, a grid
- * barrier after each, so each iteration waits at 22 grid barriers instead of 5. Starts from x = 0; the pressure zero-mean reading applies
- * to PM_OP_PRESSURE entries. autotune != 0 times the tile width (columns per tile: 16, 32, 64) x
- * block size (128, 256) on this batch once and caches the choice per size bucket.
- * Grid waits are bounded: an expired wait returns PM_TIMEOUT. The batch keeps its own workspace;
- * the operators must outlive it. count: 1..4096 systems. */
-int pm_batch_create(pm_operator* const* ops, const pm_which* which, int32_t count,
+ * with its own alpha / beta / convergence. Preconditioners: PM_PREC_JACOBI, PM_PREC_LINE,
+ * PM_PREC_IC0 (PM_PREC_NONE maps to Jacobi), opts->prec for every entry, or prec[i] per entry
+ * (prec may be NULL; an entry of PM_PREC_DEFAULT takes opts->prec), so that one batch can hold a
+ * step's IC0 velocity and mass systems next to line-preconditioned pressure systems. IC0 applies
+ * the same multicolour factor as the single-system solve: its 16 colour sweeps run as 16 phases of
+ * the persistent kernel with a grid barrier after each, so a batch holding an IC0 system waits at
+ * 22 grid barriers per iteration instead of 5. Precision: PM_FP64, or PM_FP32_REFINE (FP32
+ * difference-form values and vectors, FP64 x, dots and true-residual restarts). Starts from x = 0;
+ * the pressure zero-mean reading applies to PM_OP_PRESSURE entries. autotune != 0 times the tile
+ * width (columns per tile: 16, 32, 64) x block size (128, 256) on this batch once and caches the
+ * choice per size bucket. Grid waits are bounded: an expired wait returns PM_TIMEOUT. The batch
+ * keeps its own workspace; the operators must outlive it. count: 1..4096 systems. Errors:
+ * PM_EINVAL (null or non-symmetric entry, unknown preconditioner or precision, rtol <= 0),
+ * PM_BREAKDOWN (an IC0 factor that fails after the shift limit), PM_ENOMEM, PM_ECUDA. */
+int pm_batch_create(pm_operator* const* ops, const pm_which* which, const int32_t* prec, int32_t count,
                     const pm_solve_opts* opts, int32_t autotune, pm_batch** out, pm_stream stream);
 /* Solve all systems: b[i], x[i] device vectors of ops[i]'s length. stats: NULL or count entries.
  * Synchronises the stream. */
@@ -258,21 +265,22 @@ int pm_pcg_solve_batched(pm_operator* const* ops, const pm_which* which, const d
  * is resident, for a fixed tile_cols and block). No paper counterpart: the paper solves one basin;
  * this serves many basins' PCG solves (Section 5) at once.
  * opts: as pm_batch_create (PM_PREC_JACOBI / PM_PREC_LINE / PM_PREC_IC0 / PM_PREC_NONE; PM_FP64
- * or PM_FP32_REFINE); every system uses them. nz_cap: the largest nz admitted (sizes shared memory).
+ * or PM_FP32_REFINE); every system uses them unless its admission names its own preconditioner. nz_cap: the largest nz admitted (sizes shared memory).
  * tile_cols: 16, 32 or 64 columns per tile; block: 128 or 256 threads; blocks_per_sm: resident
  * blocks per SM of the kernel (0 = as many as fit). Errors: PM_EINVAL, PM_ENOMEM, PM_ECUDA. */
 int pm_server_create(int32_t slots, int32_t nz_cap, const pm_solve_opts* opts, int32_t tile_cols,
                      int32_t block, int32_t blocks_per_sm, pm_server** out, pm_stream stream);
 /* Device bytes of Krylov workspace one system of `op` needs at `precision` (0 for NULL). */
 size_t pm_server_workspace_bytes(const pm_operator* op, int32_t precision);
-/* Admit one system: solve A x = b for op / which from x = 0. b, x: device vectors of op's length;
+/* Admit one system: solve A x = b for op / which from x = 0, preconditioned by prec
+ * (PM_PREC_DEFAULT: the server's opts->prec). b, x: device vectors of op's length;
  * work: device workspace of at least pm_server_workspace_bytes bytes, 256-byte aligned. All three
  * are the caller's and must stay valid until the slot is returned by pm_server_poll; nothing is
  * allocated per system except when the tile array has to grow. *slot receives the slot index.
  * Errors: PM_EINVAL (non-symmetric which, nz > nz_cap, small or misaligned workspace),
  * PM_EBUSY (all slots taken), PM_ENOMEM, PM_ECUDA. Async on `stream`. */
-int pm_server_admit(pm_server* srv, pm_operator* op, pm_which which, const double* b, double* x,
-                    void* work, size_t work_bytes, int32_t* slot, pm_stream stream);
+int pm_server_admit(pm_server* srv, pm_operator* op, pm_which which, int32_t prec, const double* b,
+                    double* x, void* work, size_t work_bytes, int32_t* slot, pm_stream stream);
 /* One launch of `quantum` iterations for every resident system (systems admitted since the last
  * launch are initialised first). *active receives the number of systems still iterating.
  * Synchronises the stream. An expired grid wait returns PM_TIMEOUT (the server is then unusable:

@@ -22,6 +22,7 @@ PM_WALL_WEST, PM_WALL_EAST, PM_WALL_SOUTH, PM_WALL_NORTH = 1, 2, 4, 8
 OP_VEL_U1, OP_VEL_U2, OP_VEL_U3, OP_PRESSURE, OP_MASS = 0, 1, 2, 3, 4
 OP_VEL1_U1, OP_VEL1_U2, OP_VEL1_U3, OP_GRAD_X, OP_GRAD_Y, OP_GRAD_Z = 5, 6, 7, 8, 9, 10
 PREC_JACOBI, PREC_IC0, PREC_NONE, PREC_LINE = 0, 1, 2, 3
+PREC_DEFAULT = -1
 FP64, FP32_REFINE, BF16_REFINE = 0, 1, 2
 STEP_LUMPED, STEP_CONSISTENT = 0, 1
 KERNEL_AUTO, KERNEL_STREAM, KERNEL_RESIDENT = 0, 1, 2
@@ -100,7 +101,7 @@ SIGNATURES = {
     "pm_status_string": (ctypes.c_char_p, [_I]),
     "pm_last_error": (_I, [ctypes.c_char_p, ctypes.c_int32]),
     "pm_kernel_launch_count": (ctypes.c_int64, []),
-    "pm_batch_create": (_I, [_P, _P, ctypes.c_int32, ctypes.POINTER(SolveOpts), ctypes.c_int32,
+    "pm_batch_create": (_I, [_P, _P, _P, ctypes.c_int32, ctypes.POINTER(SolveOpts), ctypes.c_int32,
                              ctypes.POINTER(_P), _P]),
     "pm_batch_solve": (_I, [_P, _P, _P, _P, _P]),
     "pm_batch_info": (_I, [_P, _P, _P, _P, _P]),
@@ -110,7 +111,8 @@ SIGNATURES = {
     "pm_server_create": (_I, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(SolveOpts), ctypes.c_int32,
                               ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_P), _P]),
     "pm_server_workspace_bytes": (ctypes.c_size_t, [_P, ctypes.c_int32]),
-    "pm_server_admit": (_I, [_P, _P, _I, _P, _P, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int32), _P]),
+    "pm_server_admit": (_I, [_P, _P, _I, ctypes.c_int32, _P, _P, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int32),
+                             _P]),
     "pm_server_run": (_I, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), _P]),
     "pm_server_poll": (_I, [_P, _P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "pm_server_info": (_I, [_P, _P, _P, _P, _P, _P]),
@@ -417,7 +419,9 @@ class Batch:
     """A batch of independent systems solved by one persistent, graph-captured kernel (pm_batch)."""
 
     def __init__(self, ops: Sequence[Operator], which: Sequence[int], opts: Options = None,
-                 autotune: bool = False, stream=None):
+                 autotune: bool = False, stream=None, prec: Sequence[int] = None):
+        """prec: None (opts.prec for every entry) or one preconditioner per entry (PREC_DEFAULT
+        takes opts.prec)."""
         opts = opts or Options(prec=PREC_LINE)
         self.ops = list(ops)
         self.which = list(which)
@@ -425,12 +429,15 @@ class Batch:
         hops = (ctypes.c_void_p * n)(*[o.handle.value if isinstance(o.handle, ctypes.c_void_p) else o.handle
                                        for o in self.ops])
         hw = (ctypes.c_int * n)(*self.which)
+        if prec is not None and len(prec) != n:
+            raise ValueError("prec needs one entry per system")
+        hp = (ctypes.c_int32 * n)(*prec) if prec is not None else None
         o = opts.c()
         h = ctypes.c_void_p()
-        _check(load().pm_batch_create(hops, hw, n, ctypes.byref(o), 1 if autotune else 0, ctypes.byref(h),
+        _check(load().pm_batch_create(hops, hw, hp, n, ctypes.byref(o), 1 if autotune else 0, ctypes.byref(h),
                                       _stream(stream)), "batch_create")
         self.handle = h
-        self._keep = (hops, hw)
+        self._keep = (hops, hw, hp)
 
     def info(self):
         tc, blk, grid = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
@@ -484,13 +491,15 @@ class Server:
     def workspace_bytes(self, op: Operator) -> int:
         return int(load().pm_server_workspace_bytes(_handle(op.handle), self.opts.precision))
 
-    def admit(self, op: Operator, which: int, b, x, work, stream=None):
-        """Admit one system; returns its slot, or None when every slot is taken (PM_EBUSY)."""
+    def admit(self, op: Operator, which: int, b, x, work, stream=None, prec: int = None):
+        """Admit one system (prec: its preconditioner, None for the server's); returns its slot, or
+        None when every slot is taken (PM_EBUSY)."""
         torch = _torch()
         if not (work.is_cuda and work.dtype == torch.uint8 and work.is_contiguous()):
             raise ValueError("work must be a contiguous CUDA uint8 tensor")
         slot = ctypes.c_int32(-1)
-        r = load().pm_server_admit(self.handle, _handle(op.handle), which, _dptr(b, op.n, "b"), _dptr(x, op.n, "x"),
+        r = load().pm_server_admit(self.handle, _handle(op.handle), which, PREC_DEFAULT if prec is None else prec,
+                                   _dptr(b, op.n, "b"), _dptr(x, op.n, "x"),
                                    ctypes.c_void_p(work.data_ptr()), work.numel(), ctypes.byref(slot),
                                    _stream(stream))
         if r == PM_EBUSY:

@@ -2,9 +2,10 @@
 // cooperative kernel (Section 5 remark: PCG for every system of the step, here for a whole batch
 // of basins at once).
 //
-// Work is a list of tiles; a tile is up to `tile_cols` whole columns of one system, so the
-// vertical-line preconditioner can solve its columns in place. Every iteration is five phases
-// separated by a grid barrier:
+// Work is a list of tiles; a tile is whole columns of one system (at least `tile_cols`, more for
+// shallow columns), so the vertical-line preconditioner can solve its columns in place. Every
+// iteration is five phases separated by a grid barrier (IC0 systems: 16 more, one per colour
+// sweep, whose rows are dealt to blocks in colour order rather than by tile):
 //   A  tiles: w = A p and the tile partial (p, w)          | REFINE systems: FP64 r = b - A x
 //   Ar systems: alpha = rho / (p, w)                      | REFINE: true residual test
 //   B  tiles: x += alpha p, r -= alpha w, z = P^{-1} r, partials of (r, r), (r, z), m'z, 1'r
@@ -54,13 +55,15 @@ struct Sys {
   double* x;             // solution, FP64
   void *r, *p, *w, *z;   // Krylov vectors (T)
   const void* ic0F;      // T IC0 factor (colour-ordered rows, 1 / L_ii on the diagonal) or null
-  const int32_t* clsidx; // per column: index within its parity class (IC0 row positions)
-  const int32_t* coli;   // per column: grid indices (parity class)
-  const int32_t* colj;
+  const int32_t* cls_cols;  // columns listed parity class by parity class
   int64_t cbase[8];      // first colour-ordered position of each colour
+  int32_t cls_off[4];    // first entry of each parity class in cls_cols
+  int32_t cls_cnt[4];    // columns of each parity class
   int32_t nlev[2];       // levels of even / odd parity
   double one_m;
-  int32_t maskc, proj, prec, tile0, ntiles, pad;
+  int32_t maskc, proj, prec;
+  int32_t tile0, ntiles;  // the system's tiles [tile0, tile0 + ntiles) (partials, block ownership)
+  int32_t tw;             // columns per tile (the last tile may have fewer)
 };
 
 struct Scal {
@@ -70,8 +73,14 @@ struct Scal {
 };
 
 struct Tile {
-  int32_t sys, col0, ncols, pad;
+  int32_t sys, col0, ncols;
 };
+
+// Tile t of system s: columns [(t - tile0) tw, + tw) of the system, clipped to its columns.
+__device__ __forceinline__ Tile tile_of(const Sys& S, int s, int t) {
+  const int c0 = (t - S.tile0) * S.tw;
+  return Tile{s, c0, min(S.tw, S.g.ncols - c0)};
+}
 
 struct Ctl {
   uint32_t bar_count, bar_gen;
@@ -309,20 +318,21 @@ __device__ __forceinline__ void line_sweep(T* cs, const T* __restrict__ F, int c
   }
 }
 
-// One row of an IC0 colour phase (runtime colour; the same update as the single-system sweeps):
-// forward y_i = (r_i - sum_{colour(j) < c} L_ij y_j) / L_ii, backward z_i = (y_i - sum_{colour(j) > c}
-// L_ji z_j) / L_ii in place on y. The diagonal slot of F holds 1 / L_ii.
-template <typename T>
-__device__ __forceinline__ void ic0_row_rt(const Geom& g, int colour, bool fwd, int col, int k, int64_t pi,
-                                           const T* __restrict__ F, const T* r, T* y) {
+// One row of an IC0 colour phase (the same update as the single-system sweeps): forward
+// y_i = (r_i - sum_{colour(j) < C} L_ij y_j) / L_ii, backward z_i = (y_i - sum_{colour(j) > C} L_ji z_j)
+// / L_ii in place on y (natural order; pi: the row's position in colour order, its factor row).
+// F's diagonal slot holds 1 / L_ii. Returns the new y_i.
+template <typename T, int C, bool FWD>
+__device__ __forceinline__ T ic0_value(const Geom& g, int col, int k, int64_t pi, const T* __restrict__ F,
+                                       const T* r, const T* y) {
   const int nz = g.nz;
   const int64_t row = (int64_t)col * nz + k;
-  T acc = fwd ? r[row] : y[row];
+  T acc = FWD ? r[row] : y[row];
 #pragma unroll
   for (int s = 0; s < NSLOT; ++s) {
     if (s == DIAG_SLOT) continue;
-    const int cj = colour ^ slot_flip(s);
-    if (fwd ? (cj > colour) : (cj < colour)) continue;
+    const int cj = C ^ slot_flip(s);
+    if (FWD ? (cj > C) : (cj < C)) continue;
     const int kk = k + slot_dk(s);
     if (kk < 0 || kk >= nz) continue;
     const int q = slot_q(s);
@@ -330,34 +340,83 @@ __device__ __forceinline__ void ic0_row_rt(const Geom& g, int colour, bool fwd, 
     if (nb < 0) continue;
     acc = fma(-__ldg(F + (int64_t)s * g.n + pi), y[(int64_t)nb * nz + kk], acc);
   }
-  y[row] = acc * __ldg(F + (int64_t)DIAG_SLOT * g.n + pi);
+  return acc * __ldg(F + (int64_t)DIAG_SLOT * g.n + pi);
 }
 
-// The rows of one tile in one IC0 colour phase: columns of the colour's parity class, levels of
-// its parity (position = cbase[c] + index of the column in its class * levels + k / 2).
-template <typename T>
-__device__ __forceinline__ void ic0_tile(const Sys& S, const Tile& tl, int colour, bool fwd) {
-  const int kpar = colour >> 2, cls = colour & 3;
+// The rows of colour C of one system in an IC0 colour phase, in the colour-ordered enumeration of
+// the single-system sweep (position q of the colour: column cls_cols[cls_off + q / nlev], level
+// 2 (q mod nlev) + parity). Chunks of four rows per thread, all computed before any is stored;
+// block b takes the chunks ch = (b - tile0) mod G, + G, ... so that the rows of small systems
+// spread over the grid, and the block that computes a row never changes its value (no row of a
+// colour reads another row of that colour).
+template <typename T, int C, bool FWD>
+__device__ __forceinline__ void ic0_colour(const Sys& S) {
+  constexpr int kpar = C >> 2, cls = C & 3, U = 4;
   const int nlev = S.nlev[kpar];
+  const int rows = S.cls_cnt[cls] * nlev;
+  if (rows == 0) return;
+  const int G = gridDim.x, bd = blockDim.x;
+  const int chunk = U * bd;
+  const int nch = (rows + chunk - 1) / chunk;
   const T* F = (const T*)S.ic0F;
-  for (int i = threadIdx.x; i < tl.ncols * nlev; i += blockDim.x) {
-    const int col = tl.col0 + i / nlev;
-    if (((__ldg(S.coli + col) & 1) | ((__ldg(S.colj + col) & 1) << 1)) != cls) continue;
-    const int k = 2 * (i % nlev) + kpar;
-    const int64_t pi = S.cbase[colour] + (int64_t)__ldg(S.clsidx + col) * nlev + (k >> 1);
-    ic0_row_rt<T>(S.g, colour, fwd, col, k, pi, F, (const T*)S.r, (T*)S.z);
+  const T* r = (const T*)S.r;
+  T* y = (T*)S.z;
+  const int32_t* cc = S.cls_cols + S.cls_off[cls];
+  const int nz = S.g.nz;
+  const int64_t cb = S.cbase[C];
+  for (int ch = ((int)blockIdx.x - S.tile0 % G + G) % G; ch < nch; ch += G) {
+    int col[U], k[U], q[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      q[u] = ch * chunk + u * bd + (int)threadIdx.x;
+      const int qq = min(q[u], rows - 1);
+      const int t = qq / nlev;
+      k[u] = 2 * (qq - t * nlev) + kpar;
+      col[u] = __ldg(cc + t);
+      q[u] = q[u] < rows ? qq : -1;
+    }
+    T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = ic0_value<T, C, FWD>(S.g, col[u], k[u], cb + max(q[u], 0), F, r, y);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (q[u] >= 0) y[(int64_t)col[u] * nz + k[u]] = v[u];
   }
 }
 
-// Ordered list (shared memory) of the systems active in a phase, built by every block from the
-// states in one parallel pass; returns its length. Tiles a block owns in a system: t = blockIdx.x
-// mod gridDim.x within the system's range, so which block runs a tile never changes the sums.
-__device__ int phase_list(const Scal* scal, int nsys, int mode, int* list, int* wsum) {
+// Phase ph of the 16 IC0 colour phases: forward sweeps of colours 0..7, then backward 7..0.
+template <typename T>
+__device__ __forceinline__ void ic0_phase(const Sys& S, int ph) {
+  switch (ph) {
+    case 0: ic0_colour<T, 0, true>(S); break;
+    case 1: ic0_colour<T, 1, true>(S); break;
+    case 2: ic0_colour<T, 2, true>(S); break;
+    case 3: ic0_colour<T, 3, true>(S); break;
+    case 4: ic0_colour<T, 4, true>(S); break;
+    case 5: ic0_colour<T, 5, true>(S); break;
+    case 6: ic0_colour<T, 6, true>(S); break;
+    case 7: ic0_colour<T, 7, true>(S); break;
+    case 8: ic0_colour<T, 7, false>(S); break;
+    case 9: ic0_colour<T, 6, false>(S); break;
+    case 10: ic0_colour<T, 5, false>(S); break;
+    case 11: ic0_colour<T, 4, false>(S); break;
+    case 12: ic0_colour<T, 3, false>(S); break;
+    case 13: ic0_colour<T, 2, false>(S); break;
+    case 14: ic0_colour<T, 1, false>(S); break;
+    default: ic0_colour<T, 0, false>(S); break;
+  }
+}
+
+// Ordered list (shared memory) of the systems s for which want(s) holds, built by every block in
+// one parallel pass (one thread per system); returns its length. Blocks build it before each
+// phase, so that they visit only the systems they have work in, not every system in turn.
+template <typename P>
+__device__ int block_list(int nsys, P want, int* list, int* wsum) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   int base = 0;
   for (int s0 = 0; s0 < nsys; s0 += blockDim.x) {
     const int s = s0 + threadIdx.x;
-    const bool a = s < nsys && phase_active(scal[s].state, mode);
+    const bool a = s < nsys && want(s);
     const unsigned m = __ballot_sync(0xffffffffu, a);
     __syncthreads();
     if (lane == 0) wsum[wid] = __popc(m);
@@ -374,27 +433,49 @@ __device__ int phase_list(const Scal* scal, int nsys, int mode, int* list, int* 
   return base;
 }
 
+// Tiles a block owns in a system: t = blockIdx.x mod gridDim.x within the system's range, so
+// which block runs a tile never changes the sums.
 __device__ __forceinline__ int first_owned(const Sys* sys, int s) {
   const int G = gridDim.x, t0 = sys[s].tile0;
   return t0 + (((int)blockIdx.x - t0) % G + G) % G;
 }
 
-// for (t over the tiles this block owns among the systems active in MODE)
-#define FOR_OWNED_TILES(MODE, t)                                                                    \
-  for (int a_ = 0, na_ = phase_list(scal, nsys, MODE, slist, wsum); a_ < na_; ++a_)                \
-    for (int t = first_owned(sys, slist[a_]), te_ = sys[slist[a_]].tile0 + sys[slist[a_]].ntiles; \
-         t < te_; t += gridDim.x)
+// The systems active in phase MODE in which this block owns at least one tile.
+__device__ __forceinline__ int phase_list(const Scal* scal, const Sys* sys, int nsys, int mode, int* list, int* wsum) {
+  return block_list(
+      nsys, [&](int s) { return phase_active(scal[s].state, mode) && first_owned(sys, s) < sys[s].tile0 + sys[s].ntiles; },
+      list, wsum);
+}
 
-// The 16 colour phases of an IC0 apply over the tiles of the systems active in MODE (SHIFT systems
-// skipped), a grid barrier after each: a phase reads the rows the previous phases wrote in other
-// tiles. Leaves the kernel (return) when a barrier times out.
+// Whether this block has a chunk of colour c's rows in system S (the first chunk ic0_colour takes).
+__device__ __forceinline__ bool owns_ic0_chunk(const Sys& S, int c) {
+  const int rows = S.cls_cnt[c & 3] * S.nlev[c >> 2];
+  const int chunk = 4 * (int)blockDim.x, G = gridDim.x;
+  return (((int)blockIdx.x - S.tile0 % G + G) % G) < (rows + chunk - 1) / chunk;
+}
+
+// for (t over the tiles this block owns among the systems active in MODE; tl = tile t)
+#define FOR_OWNED_TILES(MODE, t, tl)                                                                \
+  for (int a_ = 0, na_ = phase_list(scal, sys, nsys, MODE, slist, wsum); a_ < na_; ++a_)           \
+    for (int t = first_owned(sys, slist[a_]), te_ = sys[slist[a_]].tile0 + sys[slist[a_]].ntiles; \
+         t < te_; t += gridDim.x)                                                                   \
+      if (const Tile tl = tile_of(sys[slist[a_]], slist[a_], t); true)
+
+// The 16 colour phases of an IC0 apply over the IC0 systems active in MODE (SHIFT systems
+// skipped), a grid barrier after each: a phase reads rows that the previous phases wrote anywhere
+// in the system. Leaves the kernel (return) when a barrier times out.
 #define IC0_PHASES(MODE)                                                                            \
   for (int ph_ = 0; ph_ < 16; ++ph_) {                                                              \
-    const int col_ = ph_ < 8 ? ph_ : 15 - ph_;                                                      \
-    FOR_OWNED_TILES(MODE, t) {                                                                      \
-      if (scal[tiles[t].sys].state == ST_SHIFT) continue;                                           \
-      ic0_tile<T>(sys[tiles[t].sys], tiles[t], col_, ph_ < 8);                                      \
-    }                                                                                               \
+    const int c_ = ph_ < 8 ? ph_ : 15 - ph_;                                                        \
+    const int na_ = block_list(                                                                     \
+        nsys,                                                                                       \
+        [&](int s) {                                                                                \
+          const int st = scal[s].state;                                                             \
+          return phase_active(st, MODE) && st != ST_SHIFT && sys[s].prec == PM_PREC_IC0 &&          \
+                 owns_ic0_chunk(sys[s], c_);                                                        \
+        },                                                                                          \
+        slist, wsum);                                                                               \
+    for (int a_ = 0; a_ < na_; ++a_) ic0_phase<T>(sys[slist[a_]], ph_);                             \
     if (!grid_barrier(ctl)) return;                                                                 \
   }
 
@@ -406,7 +487,7 @@ __device__ __forceinline__ int first_owned(const Sys* sys, int s) {
 
 template <typename T>
 __global__ void __launch_bounds__(256, PM_BATCH_MINB) k_batch(const Sys* __restrict__ sys, Scal* scal, int nsys,
-                                               const Tile* __restrict__ tiles, int ntiles, double* part, Ctl* ctl,
+                                               int ntiles, double* part, Ctl* ctl,
                                                int quantum, int init, int ic0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int* slist = reinterpret_cast<int*>(smem_raw);                             // nsys entries
@@ -420,8 +501,7 @@ __global__ void __launch_bounds__(256, PM_BATCH_MINB) k_batch(const Sys* __restr
   // batching), at the start of the next launch; systems already iterating wait at the barriers.
   if (init || *((volatile int32_t*)&ctl->pending) != 0) {
     // I1: tile partials of 1'b (pressure)
-    FOR_OWNED_TILES(3, t) {
-      const Tile tl = tiles[t];
+    FOR_OWNED_TILES(3, t, tl) {
       const Sys& S = sys[tl.sys];
       const int nz = S.g.nz, row0 = tl.col0 * nz, rows = tl.ncols * nz;
       double v[1] = {0.0};
@@ -439,8 +519,7 @@ __global__ void __launch_bounds__(256, PM_BATCH_MINB) k_batch(const Sys* __restr
     }
     if (!grid_barrier(ctl)) return;
     // I2: b' = b - lambda m; x = 0; r = b'; z = P^{-1} r (Jacobi / line) and partials
-    FOR_OWNED_TILES(3, t) {
-      const Tile tl = tiles[t];
+    FOR_OWNED_TILES(3, t, tl) {
       const Sys& S = sys[tl.sys];
       const int nz = S.g.nz, ld = nz + 1, row0 = tl.col0 * nz, rows = tl.ncols * nz;
       const double lam = scal[tl.sys].proj_c;
@@ -456,7 +535,7 @@ __global__ void __launch_bounds__(256, PM_BATCH_MINB) k_batch(const Sys* __restr
         v[0] = fma(bi, bi, v[0]);
         if (S.prec == PM_PREC_LINE) smt[(i / nz) * ld + i % nz] = (T)bi;
       }
-      if (ic0) {   // z comes from the colour phases below; the partials after them
+      if (S.prec == PM_PREC_IC0) {   // z comes from the colour phases below; the partials after them
         __syncthreads();
         continue;
       }
@@ -483,9 +562,9 @@ __global__ void __launch_bounds__(256, PM_BATCH_MINB) k_batch(const Sys* __restr
     if (!grid_barrier(ctl)) return;
     if (ic0) {
       IC0_PHASES(3)
-      FOR_OWNED_TILES(3, t) {   // partials: (b', b'), (r, z), m'z, 1'r
-        const Tile tl = tiles[t];
+      FOR_OWNED_TILES(3, t, tl) {   // partials of the IC0 systems: (b', b'), (r, z), m'z, 1'r
         const Sys& S = sys[tl.sys];
+        if (S.prec != PM_PREC_IC0) continue;
         const int nz = S.g.nz, row0 = tl.col0 * nz, rows = tl.ncols * nz;
         double v[NP] = {0.0, 0.0, 0.0, 0.0};
         for (int i = tid; i < rows; i += blockDim.x) {
@@ -531,8 +610,7 @@ __global__ void __launch_bounds__(256, PM_BATCH_MINB) k_batch(const Sys* __restr
     }
     if (!grid_barrier(ctl)) return;
     // p = z - c
-    FOR_OWNED_TILES(4, t) {
-      const Tile tl = tiles[t];
+    FOR_OWNED_TILES(4, t, tl) {
       const Sys& S = sys[tl.sys];
       const int nz = S.g.nz, row0 = tl.col0 * nz, rows = tl.ncols * nz;
       const T c = (T)scal[tl.sys].proj_c;
@@ -548,8 +626,7 @@ __global__ void __launch_bounds__(256, PM_BATCH_MINB) k_batch(const Sys* __restr
   for (int it = 0; it < quantum; ++it) {
     if (*((volatile int32_t*)&ctl->active) == 0) return;
     // ---- A: SpMV + (p, w) | REFINE: FP64 residual --------------------------------------------------
-    FOR_OWNED_TILES(0, t) {
-      const Tile tl = tiles[t];
+    FOR_OWNED_TILES(0, t, tl) {
       const Sys& S = sys[tl.sys];
       const int state = scal[tl.sys].state;
       const int nz = S.g.nz, row0 = tl.col0 * nz, rows = tl.ncols * nz;
@@ -615,8 +692,7 @@ __global__ void __launch_bounds__(256, PM_BATCH_MINB) k_batch(const Sys* __restr
     }
     if (!grid_barrier(ctl)) return;
     // ---- B: update + preconditioner + dots | RESTART: preconditioner + dots ---------------------------
-    FOR_OWNED_TILES(1, t) {
-      const Tile tl = tiles[t];
+    FOR_OWNED_TILES(1, t, tl) {
       const Sys& S = sys[tl.sys];
       const int state = scal[tl.sys].state;
       double v[NP] = {0.0, 0.0, 0.0, 0.0};
@@ -664,7 +740,7 @@ __global__ void __launch_bounds__(256, PM_BATCH_MINB) k_batch(const Sys* __restr
           }
         }
         __syncthreads();
-        if (ic0) {   // z from the colour phases after this one, (r, z), m'z, 1'r after them
+        if (S.prec == PM_PREC_IC0) {   // z from the colour phases after this one, (r, z), m'z, 1'r after them
           v[0] = acc[0].value();
           goto b_partials;
         }
@@ -716,10 +792,9 @@ __global__ void __launch_bounds__(256, PM_BATCH_MINB) k_batch(const Sys* __restr
     if (!grid_barrier(ctl)) return;
     if (ic0) {
       IC0_PHASES(1)
-      FOR_OWNED_TILES(1, t) {   // (r, z), m'z, 1'r of ITER / RESTART tiles into lanes 1..3
-        const Tile tl = tiles[t];
+      FOR_OWNED_TILES(1, t, tl) {   // (r, z), m'z, 1'r of IC0 systems' ITER / RESTART tiles into lanes 1..3
         const Sys& S = sys[tl.sys];
-        if (scal[tl.sys].state == ST_SHIFT) continue;
+        if (scal[tl.sys].state == ST_SHIFT || S.prec != PM_PREC_IC0) continue;
         const int nz = S.g.nz, row0 = tl.col0 * nz, rows = tl.ncols * nz;
         AccFor<T> acc[NP];
         for (int i = tid; i < rows; i += blockDim.x) {
@@ -798,8 +873,7 @@ __global__ void __launch_bounds__(256, PM_BATCH_MINB) k_batch(const Sys* __restr
       }
       if (tid == 0) ctl->active = act;
     }
-    FOR_OWNED_TILES(2, t) {
-      const Tile tl = tiles[t];
+    FOR_OWNED_TILES(2, t, tl) {
       const Sys& S = sys[tl.sys];
       const int nz = S.g.nz, row0 = tl.col0 * nz, rows = tl.ncols * nz;
       if (scal[tl.sys].state == ST_SHIFT2) {
@@ -845,13 +919,14 @@ struct pm_batch {
   int32_t max_iter = 100000;
   std::vector<pm_operator*> ops;
   std::vector<int32_t> which;
+  std::vector<int32_t> precs;      // preconditioner of each entry
+  bool any_ic0 = false;            // the kernel runs the IC0 colour phases
   int tile_cols = 32, block = 256, grid = 0;
   int nz_max = 0;
   int64_t ntiles = 0;
   std::vector<pm::batch::Sys> hsys;
   pm::batch::Sys* d_sys = nullptr;
   pm::batch::Scal* d_scal = nullptr;
-  pm::batch::Tile* d_tiles = nullptr;
   pm::batch::Ctl* d_ctl = nullptr;
   double* d_part = nullptr;
   void* work = nullptr;            // r, p, w, z (T) and bw (FP64) for all systems
@@ -875,23 +950,60 @@ int max_blocks(int block, size_t smem) {
   return nb;
 }
 
-// Dynamic shared memory of k_batch: the active-system list (nsys ints) and one tile of columns.
-size_t kernel_smem(int nsys, int tile_cols, int nz, int precision) {
-  const size_t es = precision == PM_FP64 ? sizeof(double) : sizeof(float);
-  return ((size_t)nsys * 4 + 15) / 16 * 16 + (size_t)tile_cols * (nz + 1) * es;
+// Columns per tile of a system with nz levels: tile_cols, widened for shallow columns toward
+// PM_TILE_ROWS_PER_THREAD rows per thread of the block (every tile visit costs a block reduction
+// of its partials and a chain of dependent loads, whatever its size; 16 measured faster than 4 on
+// the batched mass and line workloads). A line-preconditioned tile keeps at most one column per
+// thread for its sweep.
+#ifndef PM_TILE_ROWS_PER_THREAD
+#define PM_TILE_ROWS_PER_THREAD 16
+#endif
+int tile_width(int nz, int prec, int tile_cols, int block) {
+  int tc = std::max(tile_cols, (PM_TILE_ROWS_PER_THREAD * block + nz - 1) / nz);
+  if (prec == PM_PREC_LINE) tc = std::min(tc, block);
+  return tc;
 }
 
-size_t smem_bytes(const pm_batch* bt) { return kernel_smem(bt->count, bt->tile_cols, bt->nz_max, bt->precision); }
+// Dynamic shared memory: the ordered system list, and a line tile of columns (nz + 1 per column)
+// for the widest tile of any nz up to nz_max.
+size_t kernel_smem(int nsys, int tile_cols, int block, int nz_max, int precision) {
+  const size_t es = precision == PM_FP64 ? sizeof(double) : sizeof(float);
+  size_t cols = 0;
+  for (int nz = 1; nz <= nz_max; ++nz)
+    cols = std::max(cols, (size_t)tile_width(nz, PM_PREC_LINE, tile_cols, block) * (nz + 1));
+  return ((size_t)nsys * 4 + 15) / 16 * 16 + cols * es;
+}
 
-// The IC0 fields of a system descriptor: factor (FP64 or its FP32 copy), column-class index and
-// grid parities (the packed column arrays of the operator), colour bases and level counts.
-void fill_ic0(Sys* S, const pm_operator* op, int which, int prec, bool f32) {
+size_t smem_bytes(const pm_batch* bt) {
+  return kernel_smem(bt->count, bt->tile_cols, bt->block, bt->nz_max, bt->precision);
+}
+
+// Descriptor of one system: operator values (FP64, or the FP32 difference form), Jacobi
+// diagonal, the preconditioner's factors (line: Thomas factors; IC0: factor, column-class index,
+// grid parities, colour bases, level counts), mass vector. Vectors and tiles are set by the caller.
+void fill_sys(Sys* S, pm_operator* op, int w, int prec, bool f32) {
+  const int vs = which_valset(w);
+  *S = Sys{};
+  S->g = geom_of(op);
+  S->val = f32 ? (const void*)op->d_val32[vs] : (const void*)op->d_val[vs];
+  S->val64 = op->d_val[vs];
+  S->dinv = f32 ? (const void*)op->d_dinv32[w] : (const void*)op->d_dinv[w];
+  S->lineF = prec == PM_PREC_LINE ? (f32 ? (const void*)op->d_line32[w] : (const void*)op->d_line[w]) : nullptr;
+  S->m = op->d_m;
+  S->m2 = op->d_m2f;
+  S->one_m = op->one_m;
+  S->maskc = which_mask(w);
+  S->proj = w == PM_OP_PRESSURE;
+  S->prec = prec;
   S->ic0F = nullptr;
   if (prec != PM_PREC_IC0) return;
-  S->ic0F = f32 ? (const void*)op->d_ic0_32[which] : (const void*)op->ic0[which].F;
-  S->clsidx = op->d_cls_cols + op->ncols;
-  S->coli = S->clsidx + op->ncols;
-  S->colj = S->coli + op->ncols;
+  S->ic0F = f32 ? (const void*)op->d_ic0_32[w] : (const void*)op->ic0[w].F;
+  S->cls_cols = op->d_cls_cols;
+  for (int c = 0, off = 0; c < 4; ++c) {
+    S->cls_off[c] = off;
+    S->cls_cnt[c] = op->cls_count[c];
+    off += op->cls_count[c];
+  }
   S->nlev[0] = (op->nz + 1) / 2;
   S->nlev[1] = op->nz / 2;
   int64_t acc = 0;
@@ -901,18 +1013,25 @@ void fill_ic0(Sys* S, const pm_operator* op, int which, int prec, bool f32) {
   }
 }
 
+bool known_prec(int p) { return p == PM_PREC_JACOBI || p == PM_PREC_IC0 || p == PM_PREC_NONE || p == PM_PREC_LINE; }
+
+// Preconditioner of one entry: its own choice, or the default for PM_PREC_DEFAULT; NONE runs as
+// Jacobi. Both arguments are known preconditioners (or PM_PREC_DEFAULT for `given`).
+int entry_prec(int given, int dflt) {
+  const int p = given == PM_PREC_DEFAULT ? dflt : given;
+  return p == PM_PREC_NONE ? PM_PREC_JACOBI : p;
+}
+
 void free_layout(pm_batch* bt) {
   if (bt->graph) cudaGraphExecDestroy(bt->graph);
   bt->graph = nullptr;
   cudaFree(bt->d_sys);
   cudaFree(bt->d_scal);
-  cudaFree(bt->d_tiles);
   cudaFree(bt->d_ctl);
   cudaFree(bt->d_part);
   cudaFree(bt->work);
   bt->d_sys = nullptr;
   bt->d_scal = nullptr;
-  bt->d_tiles = nullptr;
   bt->d_ctl = nullptr;
   bt->d_part = nullptr;
   bt->work = nullptr;
@@ -923,7 +1042,7 @@ int build_layout(pm_batch* bt) {
   free_layout(bt);
   const bool f32 = bt->precision != PM_FP64;
   const size_t es = f32 ? sizeof(float) : sizeof(double);
-  std::vector<Tile> tiles;
+  int64_t ntiles = 0;
   bt->hsys.assign(bt->count, Sys{});
   size_t wb = 0;
   for (int s = 0; s < bt->count; ++s) wb += (size_t)bt->ops[s]->n * (4 * es + sizeof(double)) + 256 * 5;
@@ -939,45 +1058,29 @@ int build_layout(pm_batch* bt) {
   bt->nz_max = 0;
   for (int s = 0; s < bt->count; ++s) {
     pm_operator* op = bt->ops[s];
-    const int w = bt->which[s];
-    const int vs = which_valset(w);
     Sys& S = bt->hsys[s];
-    S.g = geom_of(op);
-    S.val = f32 ? (const void*)op->d_val32[vs] : (const void*)op->d_val[vs];
-    S.val64 = op->d_val[vs];
-    S.dinv = f32 ? (const void*)op->d_dinv32[w] : (const void*)op->d_dinv[w];
-    S.lineF = bt->prec == PM_PREC_LINE ? (f32 ? (const void*)op->d_line32[w] : (const void*)op->d_line[w]) : nullptr;
-    fill_ic0(&S, op, w, bt->prec, f32);
-    S.m = op->d_m;
-  S.m2 = op->d_m2f;
-    S.m2 = op->d_m2f;
-    S.one_m = op->one_m;
-    S.maskc = which_mask(w);
-    S.proj = w == PM_OP_PRESSURE;
-    S.prec = bt->prec;
+    fill_sys(&S, op, bt->which[s], bt->precs[s], f32);
     S.r = take(op->n * es);
     S.p = take(op->n * es);
     S.w = take(op->n * es);
     S.z = take(op->n * es);
     S.bw = (double*)take(op->n * sizeof(double));
-    S.tile0 = (int32_t)tiles.size();
-    for (int c0 = 0; c0 < op->ncols; c0 += bt->tile_cols) tiles.push_back(Tile{s, c0, std::min(bt->tile_cols, op->ncols - c0), 0});
-    S.ntiles = (int32_t)tiles.size() - S.tile0;
+    S.tw = tile_width(op->nz, bt->precs[s], bt->tile_cols, bt->block);
+    S.tile0 = (int32_t)ntiles;
+    S.ntiles = (op->ncols + S.tw - 1) / S.tw;
+    ntiles += S.ntiles;
     bt->nz_max = std::max(bt->nz_max, op->nz);
   }
-  bt->ntiles = (int64_t)tiles.size();
+  bt->ntiles = ntiles;
   st = cuda_check(cudaMalloc((void**)&bt->d_sys, bt->count * sizeof(Sys)), "batch sys");
   if (!st) st = cuda_check(cudaMalloc((void**)&bt->d_scal, bt->count * sizeof(Scal)), "batch scal");
-  if (!st) st = cuda_check(cudaMalloc((void**)&bt->d_tiles, tiles.size() * sizeof(Tile)), "batch tiles");
   if (!st) st = cuda_check(cudaMalloc((void**)&bt->d_ctl, sizeof(Ctl)), "batch ctl");
-  if (!st) st = cuda_check(cudaMalloc((void**)&bt->d_part, (size_t)NP * tiles.size() * sizeof(double)), "batch partials");
-  if (st) return st;
-  return cuda_check(cudaMemcpy(bt->d_tiles, tiles.data(), tiles.size() * sizeof(Tile), cudaMemcpyHostToDevice), "tiles");
+  if (!st) st = cuda_check(cudaMalloc((void**)&bt->d_part, (size_t)NP * ntiles * sizeof(double)), "batch partials");
+  return st;
 }
 
 template <typename T>
-cudaError_t launch_k(int grid, int block, size_t smem, const Sys* d_sys, Scal* d_scal, int nsys, const Tile* d_tiles,
-                     int ntiles, double* d_part, Ctl* d_ctl, int quantum, int init, int ic0, cudaStream_t s) {
+cudaError_t launch_k(int grid, int block, size_t smem, const Sys* d_sys, Scal* d_scal, int nsys, int ntiles, double* d_part, Ctl* d_ctl, int quantum, int init, int ic0, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);
@@ -989,13 +1092,13 @@ cudaError_t launch_k(int grid, int block, size_t smem, const Sys* d_sys, Scal* d
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   count_launch();
-  return cudaLaunchKernelEx(&cfg, k_batch<T>, d_sys, d_scal, nsys, d_tiles, ntiles, d_part, d_ctl, quantum, init, ic0);
+  return cudaLaunchKernelEx(&cfg, k_batch<T>, d_sys, d_scal, nsys, ntiles, d_part, d_ctl, quantum, init, ic0);
 }
 
 template <typename T>
 cudaError_t launch(pm_batch* bt, int quantum, int init, cudaStream_t s) {
-  return launch_k<T>(bt->grid, bt->block, smem_bytes(bt), bt->d_sys, bt->d_scal, (int)bt->count, bt->d_tiles,
-                     (int)bt->ntiles, bt->d_part, bt->d_ctl, quantum, init, bt->prec == PM_PREC_IC0 ? 1 : 0, s);
+  return launch_k<T>(bt->grid, bt->block, smem_bytes(bt), bt->d_sys, bt->d_scal, (int)bt->count,
+                     (int)bt->ntiles, bt->d_part, bt->d_ctl, quantum, init, bt->any_ic0 ? 1 : 0, s);
 }
 
 // Capture one launch (made by `fn` on the capture stream) into an executable graph.
@@ -1119,7 +1222,9 @@ int autotune(pm_batch* bt, cudaStream_t s) {
   for (auto* op : bt->ops) rows += op->n;
   int64_t bucket = 1;
   while (bucket < rows) bucket <<= 1;
-  TuneKey key{bucket, bt->count, bt->precision, bt->prec, bt->nz_max};
+  int prec_mask = 0;
+  for (int p : bt->precs) prec_mask |= 1 << p;
+  TuneKey key{bucket, bt->count, bt->precision, prec_mask, bt->nz_max};
   auto it = g_tuned.find(key);
   if (it != g_tuned.end()) {
     bt->tile_cols = it->second.first;
@@ -1182,13 +1287,14 @@ int autotune(pm_batch* bt, cudaStream_t s) {
 
 using namespace pm;
 
-extern "C" int pm_batch_create(pm_operator* const* ops, const pm_which* which, int32_t count,
+extern "C" int pm_batch_create(pm_operator* const* ops, const pm_which* which, const int32_t* prec, int32_t count,
                                const pm_solve_opts* opts, int32_t autotune, pm_batch** out, pm_stream stream) {
   if (!ops || !which || !opts || !out || count <= 0 || count > 4096) return set_error(PM_EINVAL, "bad batch arguments");
   *out = nullptr;
-  if (opts->prec != PM_PREC_JACOBI && opts->prec != PM_PREC_LINE && opts->prec != PM_PREC_NONE &&
-      opts->prec != PM_PREC_IC0)
-    return set_error(PM_EINVAL, "unknown preconditioner");
+  if (!batch::known_prec(opts->prec)) return set_error(PM_EINVAL, "unknown preconditioner");
+  for (int i = 0; prec && i < count; ++i)
+    if (prec[i] != PM_PREC_DEFAULT && !batch::known_prec(prec[i]))
+      return set_error(PM_EINVAL, "unknown preconditioner in the per-entry list");
   if (opts->precision != PM_FP64 && opts->precision != PM_FP32_REFINE)
     return set_error(PM_EINVAL, "batched PCG supports PM_FP64 and PM_FP32_REFINE");
   if (!(opts->rtol > 0.0)) return set_error(PM_EINVAL, "rtol must be > 0");
@@ -1206,13 +1312,16 @@ extern "C" int pm_batch_create(pm_operator* const* ops, const pm_which* which, i
       delete bt;
       return set_error(PM_EINVAL, "batch entry with a null or non-symmetric operator");
     }
-    int st = prepare_for_batch(ops[i], (int)which[i], bt->prec, bt->precision, s);
+    const int pi = batch::entry_prec(prec ? prec[i] : PM_PREC_DEFAULT, bt->prec);
+    int st = prepare_for_batch(ops[i], (int)which[i], pi, bt->precision, s);
     if (st) {
       delete bt;
       return st;
     }
     bt->ops.push_back(ops[i]);
     bt->which.push_back((int32_t)which[i]);
+    bt->precs.push_back(pi);
+    bt->any_ic0 = bt->any_ic0 || pi == PM_PREC_IC0;
   }
   int st = cuda_check(cudaStreamSynchronize(s), "batch preparation");
   if (!st && autotune) st = batch::autotune(bt, s);
@@ -1264,7 +1373,7 @@ extern "C" int pm_pcg_solve_batched(pm_operator* const* ops, const pm_which* whi
                                     double* const* x, int32_t count, const pm_solve_opts* opts,
                                     pm_solve_stats* stats, pm_stream stream) {
   pm_batch* bt = nullptr;
-  int st = pm_batch_create(ops, which, count, opts, 0, &bt, stream);
+  int st = pm_batch_create(ops, which, nullptr, count, opts, 0, &bt, stream);
   if (st) return st;
   st = pm_batch_solve(bt, b, x, stats, stream);
   pm_batch_destroy(bt);
@@ -1288,13 +1397,14 @@ struct pm_server {
   std::vector<pm::batch::Sys> hsys;
   std::vector<pm_operator*> ops;
   std::vector<int32_t> which;
+  std::vector<int32_t> precs;   // preconditioner of each slot's system
+  int32_t n_ic0 = 0;            // used slots with IC0: the kernel runs the colour phases
+  int graph_ic0 = 0;
   std::vector<uint8_t> used;
   std::vector<int64_t> tile0, ntiles;
-  std::vector<pm::batch::Tile> htiles;
   int64_t tcap = 0;
   pm::batch::Sys* d_sys = nullptr;
   pm::batch::Scal* d_scal = nullptr;
-  pm::batch::Tile* d_tiles = nullptr;
   pm::batch::Ctl* d_ctl = nullptr;
   double* d_part = nullptr;
   pm::batch::Scal* h_scal = nullptr;  // pinned mirror, refreshed after every launch
@@ -1310,42 +1420,34 @@ namespace pm {
 namespace batch {
 namespace {
 
-size_t server_smem(const pm_server* sv) { return kernel_smem(sv->cap, sv->tile_cols, sv->nz_cap, sv->precision); }
+size_t server_smem(const pm_server* sv) {
+  return kernel_smem(sv->cap, sv->tile_cols, sv->block, sv->nz_cap, sv->precision);
+}
 
 void server_free(pm_server* sv) {
   if (sv->graph) cudaGraphExecDestroy(sv->graph);
   cudaFree(sv->d_sys);
   cudaFree(sv->d_scal);
-  cudaFree(sv->d_tiles);
   cudaFree(sv->d_ctl);
   cudaFree(sv->d_part);
   cudaFreeHost(sv->h_scal);
   cudaFreeHost(sv->h_ctl);
 }
 
-// Tile array capacity >= want: reallocate tiles and partials (contents of the partials need not
-// survive a launch boundary), re-upload the host tile mirror; the graph is re-captured later.
+// Tile capacity >= want: reallocate the partials (their contents need not survive a launch
+// boundary); the graph is re-captured later.
 int server_grow_tiles(pm_server* sv, int64_t want) {
   if (want <= sv->tcap) return PM_OK;
   int64_t nc = std::max<int64_t>(sv->tcap * 2, 1024);
   while (nc < want) nc *= 2;
   if (nc > (int64_t)1 << 30) return set_error(PM_ENOMEM, "server tile array too large");
-  Tile* nt = nullptr;
   double* np = nullptr;
-  int st = cuda_check(cudaMalloc((void**)&nt, nc * sizeof(Tile)), "server tiles");
-  if (!st) st = cuda_check(cudaMalloc((void**)&np, (size_t)NP * nc * sizeof(double)), "server partials");
-  if (st) {
-    cudaFree(nt);
-    return st;
-  }
-  sv->htiles.resize(nc, Tile{0, 0, 0, 0});
-  st = cuda_check(cudaMemcpy(nt, sv->htiles.data(), nc * sizeof(Tile), cudaMemcpyHostToDevice), "server tiles");
-  cudaFree(sv->d_tiles);
+  const int st = cuda_check(cudaMalloc((void**)&np, (size_t)NP * nc * sizeof(double)), "server partials");
+  if (st) return st;
   cudaFree(sv->d_part);
-  sv->d_tiles = nt;
   sv->d_part = np;
   sv->tcap = nc;
-  return st;
+  return PM_OK;
 }
 
 // First-fit tile range of `need` tiles among the occupied slots' ranges; grows the array if none.
@@ -1384,9 +1486,7 @@ extern "C" int pm_server_create(int32_t slots, int32_t nz_cap, const pm_solve_op
   if (!opts || !out || slots <= 0 || slots > 4096 || nz_cap < 2 || nz_cap > 4096)
     return set_error(PM_EINVAL, "bad server arguments");
   *out = nullptr;
-  if (opts->prec != PM_PREC_JACOBI && opts->prec != PM_PREC_LINE && opts->prec != PM_PREC_NONE &&
-      opts->prec != PM_PREC_IC0)
-    return set_error(PM_EINVAL, "unknown preconditioner");
+  if (!known_prec(opts->prec)) return set_error(PM_EINVAL, "unknown preconditioner");
   if (opts->precision != PM_FP64 && opts->precision != PM_FP32_REFINE)
     return set_error(PM_EINVAL, "server supports PM_FP64 and PM_FP32_REFINE");
   if (!(opts->rtol > 0.0)) return set_error(PM_EINVAL, "rtol must be > 0");
@@ -1407,6 +1507,7 @@ extern "C" int pm_server_create(int32_t slots, int32_t nz_cap, const pm_solve_op
   sv->hsys.assign(slots, Sys{});
   sv->ops.assign(slots, nullptr);
   sv->which.assign(slots, 0);
+  sv->precs.assign(slots, 0);
   sv->used.assign(slots, 0);
   sv->tile0.assign(slots, 0);
   sv->ntiles.assign(slots, 0);
@@ -1448,11 +1549,13 @@ extern "C" int pm_server_create(int32_t slots, int32_t nz_cap, const pm_solve_op
   return PM_OK;
 }
 
-extern "C" int pm_server_admit(pm_server* sv, pm_operator* op, pm_which which, const double* b, double* x,
-                               void* work, size_t work_bytes, int32_t* slot, pm_stream stream) {
+extern "C" int pm_server_admit(pm_server* sv, pm_operator* op, pm_which which, int32_t prec, const double* b,
+                               double* x, void* work, size_t work_bytes, int32_t* slot, pm_stream stream) {
   using namespace pm::batch;
   if (!sv || !op || !b || !x || !work || !slot) return set_error(PM_EINVAL, "null server argument");
   *slot = -1;
+  if (prec != PM_PREC_DEFAULT && !known_prec(prec)) return set_error(PM_EINVAL, "unknown preconditioner");
+  const int pi = entry_prec(prec, sv->prec);
   if (!which_symmetric((int)which)) return set_error(PM_EINVAL, "server entry with a non-symmetric operator");
   if (op->nz > sv->nz_cap) return set_error(PM_EINVAL, "operator has more levels than the server's nz_cap");
   if (work_bytes < pm_server_workspace_bytes(op, sv->precision)) return set_error(PM_EINVAL, "workspace too small");
@@ -1465,18 +1568,14 @@ extern "C" int pm_server_admit(pm_server* sv, pm_operator* op, pm_which which, c
     }
   if (s_i < 0) return set_error(PM_EBUSY, "no free server slot");
   cudaStream_t s = (cudaStream_t)stream;
-  int st = prepare_for_batch(op, (int)which, sv->prec, sv->precision, s);
+  int st = prepare_for_batch(op, (int)which, pi, sv->precision, s);
   if (st) return st;
-  const int64_t need = (op->ncols + sv->tile_cols - 1) / sv->tile_cols;
+  const int tw = tile_width(op->nz, pi, sv->tile_cols, sv->block);
+  const int64_t need = (op->ncols + tw - 1) / tw;
   int64_t t0 = 0;
   if ((st = server_tile_range(sv, need, &t0))) return st;
-  for (int64_t t = 0; t < need; ++t) {
-    const int c0 = (int)t * sv->tile_cols;
-    sv->htiles[t0 + t] = Tile{s_i, c0, std::min(sv->tile_cols, op->ncols - c0), 0};
-  }
   const bool f32 = sv->precision != PM_FP64;
   const size_t es = f32 ? sizeof(float) : sizeof(double);
-  const int w = (int)which, vs = which_valset(w);
   char* cur = (char*)work;
   auto take = [&](size_t bytes) {
     void* p = cur;
@@ -1484,19 +1583,7 @@ extern "C" int pm_server_admit(pm_server* sv, pm_operator* op, pm_which which, c
     return p;
   };
   Sys& S = sv->hsys[s_i];
-  S = Sys{};
-  S.g = geom_of(op);
-  S.val = f32 ? (const void*)op->d_val32[vs] : (const void*)op->d_val[vs];
-  S.val64 = op->d_val[vs];
-  S.dinv = f32 ? (const void*)op->d_dinv32[w] : (const void*)op->d_dinv[w];
-  S.lineF = sv->prec == PM_PREC_LINE ? (f32 ? (const void*)op->d_line32[w] : (const void*)op->d_line[w]) : nullptr;
-  fill_ic0(&S, op, w, sv->prec, f32);
-  S.m = op->d_m;
-  S.m2 = op->d_m2f;
-  S.one_m = op->one_m;
-  S.maskc = which_mask(w);
-  S.proj = w == PM_OP_PRESSURE;
-  S.prec = sv->prec;
+  fill_sys(&S, op, (int)which, pi, f32);
   S.r = take(op->n * es);
   S.p = take(op->n * es);
   S.w = take(op->n * es);
@@ -1506,20 +1593,22 @@ extern "C" int pm_server_admit(pm_server* sv, pm_operator* op, pm_which which, c
   S.x = x;
   S.tile0 = (int32_t)t0;
   S.ntiles = (int32_t)need;
+  S.tw = tw;
   Scal c;
   std::memset(&c, 0, sizeof(c));
   c.rtol = sv->rtol;
   c.inner_rtol = sv->inner_rtol;
   c.max_iter = sv->max_iter;
   c.state = ST_NEW;
-  st = cuda_check(cudaMemcpyAsync(sv->d_tiles + t0, sv->htiles.data() + t0, need * sizeof(Tile), cudaMemcpyHostToDevice, s), "tiles");
-  if (!st) st = cuda_check(cudaMemcpyAsync(sv->d_sys + s_i, &S, sizeof(Sys), cudaMemcpyHostToDevice, s), "sys");
+  st = cuda_check(cudaMemcpyAsync(sv->d_sys + s_i, &S, sizeof(Sys), cudaMemcpyHostToDevice, s), "sys");
   if (!st) st = cuda_check(cudaMemcpyAsync(sv->d_scal + s_i, &c, sizeof(Scal), cudaMemcpyHostToDevice, s), "scal");
   if (st) return st;
   sv->h_scal[s_i] = c;
   sv->used[s_i] = 1;
   sv->ops[s_i] = op;
   sv->which[s_i] = (int32_t)which;
+  sv->precs[s_i] = pi;
+  sv->n_ic0 += pi == PM_PREC_IC0;
   sv->tile0[s_i] = t0;
   sv->ntiles[s_i] = need;
   sv->pending += 1;
@@ -1545,18 +1634,20 @@ extern "C" int pm_server_run(pm_server* sv, int32_t quantum, int32_t* active, pm
                                     cudaMemcpyHostToDevice, s), "ctl");
     if (st) return st;
   }
-  if (!sv->graph || sv->graph_quantum != quantum || sv->graph_tcap != sv->tcap) {
+  const int ic0 = sv->n_ic0 > 0 ? 1 : 0;
+  if (!sv->graph || sv->graph_quantum != quantum || sv->graph_tcap != sv->tcap || sv->graph_ic0 != ic0) {
     const size_t smem = server_smem(sv);
     st = capture_graph(&sv->graph, [&](cudaStream_t cs) {
       return sv->precision == PM_FP64
-                 ? launch_k<double>(sv->grid, sv->block, smem, sv->d_sys, sv->d_scal, sv->cap, sv->d_tiles,
-                                    (int)sv->tcap, sv->d_part, sv->d_ctl, quantum, 0, sv->prec == PM_PREC_IC0 ? 1 : 0, cs)
-                 : launch_k<float>(sv->grid, sv->block, smem, sv->d_sys, sv->d_scal, sv->cap, sv->d_tiles,
-                                   (int)sv->tcap, sv->d_part, sv->d_ctl, quantum, 0, sv->prec == PM_PREC_IC0 ? 1 : 0, cs);
+                 ? launch_k<double>(sv->grid, sv->block, smem, sv->d_sys, sv->d_scal, sv->cap,
+                                    (int)sv->tcap, sv->d_part, sv->d_ctl, quantum, 0, ic0, cs)
+                 : launch_k<float>(sv->grid, sv->block, smem, sv->d_sys, sv->d_scal, sv->cap,
+                                   (int)sv->tcap, sv->d_part, sv->d_ctl, quantum, 0, ic0, cs);
     });
     if (st) return st;
     sv->graph_quantum = quantum;
     sv->graph_tcap = sv->tcap;
+    sv->graph_ic0 = ic0;
   }
   st = cuda_check(cudaGraphLaunch(sv->graph, s), "server graph launch");
   if (st) return st;
@@ -1597,6 +1688,7 @@ extern "C" int pm_server_poll(pm_server* sv, int32_t* slots, pm_solve_stats* sta
       o.bytes_moved = c.iter * nr * (15 * es + 11 * es + 8 + 8) + c.outer * nr * (15 * 8 + 24);
     }
     sv->used[i] = 0;
+    sv->n_ic0 -= sv->precs[i] == PM_PREC_IC0;
     sv->ops[i] = nullptr;
     sv->ntiles[i] = 0;
     ++n;

@@ -12,7 +12,9 @@ served by one loop:
     are released after its last one.
 Right-hand side j of a request is the system of the projection step it stands for: the three
 velocity components (j = 0, 1, 2; Eq. fofa_velo_pred_h) and the pressure increment (j = 3;
-Eq. fofa_q_cor_h).
+Eq. fofa_q_cor_h). With the consistent-mass velocity correction (Eq. fofa_velo_cor_h solved with
+M rather than its lumped diagonal) a step has three more systems, M u_c = rhs_c (j = 4, 5, 6),
+served with IC0 next to the others in the same persistent kernel.
 
 The loop talks to a backend (the GPU one below, or a host fake in tests), so the scheduling logic
 is the same code whichever runs the solves. `serial` mode is the plain baseline: requests in
@@ -28,6 +30,7 @@ from typing import Dict, List, Optional, Sequence
 import numpy as np
 
 RHS_WHICH = (0, 1, 2, 3)  # OP_VEL_U1, OP_VEL_U2, OP_VEL_U3, OP_PRESSURE
+RHS_WHICH_CONSISTENT = RHS_WHICH + (4, 4, 4)  # and OP_MASS for each velocity component
 
 
 @dataclass
@@ -235,12 +238,21 @@ class GpuBackend:
     """Backend on the resident server (continuous) or on the single-system solver (serial)."""
 
     def __init__(self, opts=None, slots: int = 64, nz_cap: int = 64, tile_cols: int = 64, block: int = 128,
-                 blocks_per_sm: int = 0, serial_opts=None, rhs: str = "device", keep=None):
+                 blocks_per_sm: int = 0, serial_opts=None, rhs: str = "device", keep=None,
+                 correction: str = "lumped"):
+        import dataclasses
+
         import torch
 
         from . import api
+        if correction not in ("lumped", "consistent"):
+            raise ValueError("correction must be 'lumped' or 'consistent'")
         self.torch = torch
         self.api = api
+        self.which = RHS_WHICH if correction == "lumped" else RHS_WHICH_CONSISTENT
+        # the mass systems take IC0; the others the server's (and the serial path's) preconditioner
+        self.prec = [None if w != api.OP_MASS else api.PREC_IC0 for w in self.which]
+        self._replace = dataclasses.replace
         # FP32 inner solves restarted from the FP64 residual every four orders of magnitude
         self.opts = opts or api.Options(prec=api.PREC_LINE, precision=api.FP32_REFINE, rtol=1e-8, inner_rtol=1e-4,
                                         max_iter=200000)
@@ -285,8 +297,9 @@ class GpuBackend:
 
     def session_bytes(self, session):
         n = session.side * session.side * session.nz
-        # operators + 4 systems x (x, b, workspace) + low-precision copies and line factors
-        return self.api.operator_bytes(self._basin(session)) + n * (4 * (8 + 8 + 40) + 320)
+        # operators + one (x, b, workspace) per system + low-precision copies, line and IC0 factors
+        return self.api.operator_bytes(self._basin(session)) + n * (len(self.which) * (8 + 8 + 40) + 320 +
+                                                                    (180 if len(self.which) > 4 else 0))
 
     def open_session(self, sid, session):
         t0 = time.perf_counter()
@@ -300,9 +313,9 @@ class GpuBackend:
         n = op.n
         ws = int(self.api.load().pm_server_workspace_bytes(self.api._handle(op.handle), self.opts.precision))
         h = {"sid": sid, "op": op,
-             "x": [torch.zeros(n, dtype=torch.float64, device="cuda") for _ in RHS_WHICH],
-             "b": [torch.empty(n, dtype=torch.float64, device="cuda") for _ in RHS_WHICH],
-             "work": [torch.empty(ws, dtype=torch.uint8, device="cuda") for _ in RHS_WHICH]}
+             "x": [torch.zeros(n, dtype=torch.float64, device="cuda") for _ in self.which],
+             "b": [torch.empty(n, dtype=torch.float64, device="cuda") for _ in self.which],
+             "work": [torch.empty(ws, dtype=torch.uint8, device="cuda") for _ in self.which]}
         return h
 
     def close_session(self, h):
@@ -328,7 +341,7 @@ class GpuBackend:
     def admit(self, h, j, seed, key):
         b = self._fill_rhs(h, j, seed)
         t0 = time.perf_counter()
-        s = self._srv().admit(h["op"], RHS_WHICH[j], b, h["x"][j], h["work"][j])
+        s = self._srv().admit(h["op"], self.which[j], b, h["x"][j], h["work"][j], prec=self.prec[j])
         if s is not None:
             self._slot_key[s] = (key, h, j)
         self._t("admit", t0)
@@ -356,7 +369,8 @@ class GpuBackend:
         b = self._fill_rhs(h, j, seed)
         x = h["x"][j]
         t0 = time.perf_counter()
-        st = h["op"].solve(RHS_WHICH[j], b, x, self.serial_opts, allow_not_converged=True)
+        opts = self.serial_opts if self.prec[j] is None else self._replace(self.serial_opts, prec=self.prec[j])
+        st = h["op"].solve(self.which[j], b, x, opts, allow_not_converged=True)
         self._t("solve", t0)
         if key in self.keep:
             self.kept[key] = x.cpu().numpy().copy()

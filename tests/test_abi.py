@@ -116,12 +116,13 @@ def test_server_and_batch_validation_without_gpu(lib_path):
         a = {**good, **b}
         assert lib.pm_server_create(a["slots"], a["nz_cap"], opts(), a["tile_cols"], a["block"], a["bps"],
                                     ctypes.byref(out), None) == api.PM_EINVAL, b
-    for o in (opts(prec=api.PREC_IC0), opts(precision=api.BF16_REFINE), opts(rtol=0.0)):
+    for o in (opts(prec=7), opts(prec=-1), opts(precision=api.BF16_REFINE), opts(rtol=0.0)):
         assert lib.pm_server_create(8, 32, o, 64, 128, 0, ctypes.byref(out), None) == api.PM_EINVAL
     assert lib.pm_server_create(8, 32, None, 64, 128, 0, ctypes.byref(out), None) == api.PM_EINVAL
     assert lib.pm_server_workspace_bytes(None, api.FP64) == 0
     slot = ctypes.c_int32()
-    assert lib.pm_server_admit(None, None, 0, None, None, None, 0, ctypes.byref(slot), None) == api.PM_EINVAL
+    assert lib.pm_server_admit(None, None, 0, api.PREC_DEFAULT, None, None, None, 0, ctypes.byref(slot),
+                               None) == api.PM_EINVAL
     act = ctypes.c_int32()
     assert lib.pm_server_run(None, 16, ctypes.byref(act), None) == api.PM_EINVAL
     n = ctypes.c_int32()
@@ -132,9 +133,12 @@ def test_server_and_batch_validation_without_gpu(lib_path):
 
     ops = (ctypes.c_void_p * 2)(None, None)
     which = (ctypes.c_int * 2)(0, 3)
-    for count, o in ((0, opts()), (5000, opts()), (2, opts(prec=api.PREC_IC0)), (2, opts(precision=api.BF16_REFINE)),
+    for count, o in ((0, opts()), (5000, opts()), (2, opts(prec=7)), (2, opts(precision=api.BF16_REFINE)),
                      (2, opts(rtol=-1.0))):
-        assert lib.pm_batch_create(ops, which, count, o, 0, ctypes.byref(out), None) == api.PM_EINVAL
+        assert lib.pm_batch_create(ops, which, None, count, o, 0, ctypes.byref(out), None) == api.PM_EINVAL
+    for bad in ((0, 9), (0, -2)):    # unknown per-entry preconditioners
+        pr = (ctypes.c_int32 * 2)(*bad)
+        assert lib.pm_batch_create(ops, which, pr, 2, opts(), 0, ctypes.byref(out), None) == api.PM_EINVAL
     assert lib.pm_batch_solve(None, None, None, None, None) == api.PM_EINVAL
     assert lib.pm_batch_info(None, None, None, None, None) == api.PM_EINVAL
     lib.pm_batch_destroy(None)

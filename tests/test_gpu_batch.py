@@ -72,12 +72,13 @@ def seed_of(entry):
     return 40 + (ENTRIES + MASS_ENTRIES).index(entry)
 
 
-def run_batch(entries, prec, precision=pm.FP64, rtol=1e-12, autotune=False):
+def run_batch(entries, prec, precision=pm.FP64, rtol=1e-12, autotune=False, per_entry=None):
     opsl = [case(nm)[1] for nm, _ in entries]
     bs = [torch.from_numpy(rhs_for(nm, w, seed_of((nm, w)))).cuda() for nm, w in entries]
     xs = [torch.zeros_like(b) for b in bs]
     batch = pm.Batch(opsl, [w for _, w in entries], pm.Options(rtol=rtol, prec=prec, precision=precision,
-                                                               max_iter=200000), autotune=autotune)
+                                                               max_iter=200000), autotune=autotune,
+                     prec=per_entry)
     stats = batch.solve(bs, xs)
     info = batch.info()
     batch.close()
@@ -132,6 +133,40 @@ def test_batch_mixed_precision(prec):
         rhs = rhs_for(nm, w, seed_of((nm, w)))
         ref = oracle_solve(ops, w, rhs, pm.PREC_JACOBI, 1e-12 if w == pm.OP_PRESSURE else 1e-13)
         assert np.linalg.norm(x - ref.x) <= 1e-5 * np.linalg.norm(ref.x), (nm, w)
+
+
+def paper_precs(entries):
+    """The paper's choice per system: IC0 for the velocity and mass systems; the pressure here
+    takes the vertical-line preconditioner."""
+    return [pm.PREC_LINE if w == pm.OP_PRESSURE else pm.PREC_IC0 for _, w in entries]
+
+
+@pytest.mark.parametrize("precision", [pm.FP64, pm.FP32_REFINE])
+def test_batch_with_a_preconditioner_per_system(precision):
+    """One batch holding IC0 velocity and mass systems next to line-preconditioned pressure
+    systems: each system gives the bits it gives in a batch of its own preconditioner, and
+    matches its solo solve."""
+    entries = ENTRIES + MASS_ENTRIES
+    precs = paper_precs(entries)
+    rtol = 1e-12 if precision == pm.FP64 else 1e-8
+    xs, stats, _ = run_batch(entries, pm.PREC_JACOBI, precision=precision, rtol=rtol, per_entry=precs)
+    for p in (pm.PREC_IC0, pm.PREC_LINE):
+        sub = [e for e, q in zip(entries, precs) if q == p]
+        xs_p, st_p, _ = run_batch(sub, p, precision=precision, rtol=rtol)
+        for e, x, st in zip(sub, xs_p, st_p):
+            i = entries.index(e)
+            assert np.array_equal(xs[i], x), e
+            assert stats[i].iters == st.iters, e
+    for (nm, w), x, st, p in zip(entries, xs, stats, precs):
+        b, op, ops = case(nm)
+        assert st.status == pm.PM_OK, (nm, w)
+        if precision == pm.FP64:
+            rhs = rhs_for(nm, w, seed_of((nm, w)))
+            xd = torch.zeros(op.n, dtype=torch.float64, device="cuda")
+            solo = op.solve(w, torch.from_numpy(rhs).cuda(), xd, pm.Options(rtol=1e-12, prec=p, max_restarts=5),
+                            allow_not_converged=True)
+            assert np.linalg.norm(x - xd.cpu().numpy()) <= 1e-9 * np.linalg.norm(xd.cpu().numpy()), (nm, w)
+            assert abs(st.first_pass_iters - solo.first_pass_iters) <= max(2, 0.02 * solo.first_pass_iters)
 
 
 def test_batch_autotune_picks_a_shape():

@@ -62,6 +62,50 @@ def test_staggered_admission_matches_one_shot_batch(precision, prec):
         assert np.array_equal(xs[i].cpu().numpy(), ref_x[i]), ENTRIES[i]
 
 
+def test_server_admission_with_its_own_preconditioner():
+    """Systems admitted with their own preconditioners (IC0 velocity and mass, line pressure) give
+    the bits of the one-shot batch built with the same per-system list."""
+    from test_gpu_batch import MASS_ENTRIES, paper_precs
+    entries = ENTRIES + MASS_ENTRIES
+    precs = paper_precs(entries)
+    ref_x, ref_st, info = run_batch(entries, pm.PREC_JACOBI, rtol=1e-10, per_entry=precs)
+    srv = pm.Server(slots=16, nz_cap=16, opts=pm.Options(rtol=1e-10, prec=pm.PREC_JACOBI, max_iter=200000),
+                    tile_cols=info["tile_cols"], block=info["block"])
+    xs, slot_of, stats = [], {}, {}
+    keep = []
+    for i, ((nm, w), p) in enumerate(zip(entries, precs)):
+        op = case(nm)[1]
+        b = torch.from_numpy(rhs_for(nm, w, seed_of((nm, w)))).cuda()
+        x = torch.zeros(op.n, dtype=torch.float64, device="cuda")
+        ws = torch.empty(srv.workspace_bytes(op), dtype=torch.uint8, device="cuda")
+        keep.append((b, ws))
+        xs.append(x)
+        s = srv.admit(op, w, b, x, ws, prec=p)
+        slot_of[s] = i
+        if i == 5:       # the rest join while the first ones iterate
+            srv.run(4)
+            for s2, st in srv.poll():
+                stats[slot_of.pop(s2)] = st
+    while slot_of:
+        srv.run(16)
+        for s, st in srv.poll():
+            stats[slot_of.pop(s)] = st
+    srv.close()
+    for i, e in enumerate(entries):
+        assert stats[i].status == pm.PM_OK, e
+        assert stats[i].iters == ref_st[i].iters, e
+        assert np.array_equal(xs[i].cpu().numpy(), ref_x[i]), e
+    with pytest.raises(pm.PMError):
+        srv2 = pm.Server(slots=2, nz_cap=16)
+        try:
+            op = case("box16")[1]
+            b = torch.zeros(op.n, dtype=torch.float64, device="cuda")
+            srv2.admit(op, pm.OP_VEL_U1, b, torch.zeros_like(b),
+                       torch.empty(srv2.workspace_bytes(op), dtype=torch.uint8, device="cuda"), prec=9)
+        finally:
+            srv2.close()
+
+
 def small_stream():
     sessions = [Session(side=12, nz=8, seed=11), Session(side=16, nz=10, seed=12), Session(side=10, nz=12, seed=13),
                 Session(side=14, nz=9, seed=14)]
@@ -148,3 +192,29 @@ def test_server_slot_and_argument_errors():
         srv2.admit(deep, pm.OP_PRESSURE, xd, xd, wd)
     assert ei.value.status == pm.PM_EINVAL  # nz 12 > nz_cap 8
     srv2.close()
+
+
+def test_consistent_mass_correction_is_served_with_ic0():
+    """A step with the consistent-mass velocity correction is seven systems: the mass systems
+    (j = 4, 5, 6) join the same persistent kernel with IC0 while the others keep the line
+    preconditioner. Continuous and serial serving agree, and the mass solutions match the oracle's
+    M^{-1} rhs."""
+    sessions, reqs = small_stream()
+    reqs = [Request(t_arrival=r.t_arrival, session=r.session, step=r.step, nrhs=7, rhs_seed=r.rhs_seed)
+            for r in reqs[:4]]
+    keys = [(i, j) for i in range(4) for j in range(7)]
+    a = GpuBackend(slots=32, nz_cap=16, rhs="host", keep=keys, correction="consistent")
+    rep = Scheduler(a, sessions, reqs, slots=32, quantum=4).run()
+    a.close()
+    assert all(s == pm.PM_OK for r in rep.records for s in r.status)
+    assert all(r.iters[j] < 40 for r in rep.records for j in (4, 5, 6)), [r.iters for r in rep.records]
+    b = GpuBackend(slots=32, nz_cap=16, rhs="host", keep=keys, correction="consistent")
+    Scheduler(b, sessions, reqs, slots=32, mode="serial").run()
+    for k in keys:
+        assert np.linalg.norm(a.kept[k] - b.kept[k]) <= 1e-5 * np.linalg.norm(b.kept[k]), k
+    s0 = sessions[reqs[0].session]
+    ops = fem.assemble(box_basin(nh=s0.side, nz=s0.nz, seed=s0.seed))
+    for j in (4, 5, 6):
+        rhs = random_vector(ops.mesh.n, reqs[0].rhs_seed + j)
+        ref = opcg.pcg(ops.M, rhs, rtol=1e-13, precond=opcg.ic0_preconditioner(ops.M, ops.mesh.colour)[0]).x
+        assert np.linalg.norm(a.kept[(0, j)] - ref) <= 1e-6 * np.linalg.norm(ref), j

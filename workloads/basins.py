@@ -189,13 +189,15 @@ class Session:
 
 def request_stream(seed: int = 1207, rate: float = 200.0, n_requests: int = 2000,
                    concurrent_sessions: int = 8, steps_per_session: int = 100,
-                   median_nodes: float = 1.5e5, sigma: float = 1.0, max_nodes: float = 8e6):
+                   median_nodes: float = 1.5e5, sigma: float = 1.0, max_nodes: float = 8e6,
+                   max_rhs: int = 4):
     """Poisson arrivals of solve requests (rate per second) over basins with lognormal node counts.
 
     Each session is one box basin that issues `steps_per_session` consecutive requests; requests
     are dealt round-robin to `concurrent_sessions` open sessions, and a finished session is
     replaced by a new basin. A basin draws n ~ lognormal(median, sigma) clipped to max_nodes,
-    nz in U{8..48} and side sqrt(n / nz). Each request carries 1-4 right-hand sides.
+    nz in U{8..48} and side sqrt(n / nz). Each request carries 1..max_rhs right-hand sides (4: the
+    systems of a step with the lumped correction; 7 with the consistent-mass one).
     Returns (sessions, requests).
     """
     rng = np.random.default_rng(seed)
@@ -216,7 +218,7 @@ def request_stream(seed: int = 1207, rate: float = 200.0, n_requests: int = 2000
         t += float(rng.exponential(1.0 / rate))
         slot = q % concurrent_sessions
         s = open_s[slot]
-        reqs.append(Request(t_arrival=t, session=s, step=used[s], nrhs=int(rng.integers(1, 5)),
+        reqs.append(Request(t_arrival=t, session=s, step=used[s], nrhs=int(rng.integers(1, max_rhs + 1)),
                             rhs_seed=int(rng.integers(0, 2 ** 31 - 1))))
         used[s] += 1
         if used[s] >= steps_per_session:
