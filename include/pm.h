@@ -50,7 +50,8 @@ enum {
   PM_BREAKDOWN = 5,     /* (p, Ap) <= 0 or non-finite, or IC0 pivot failure after 11 shifts    */
   PM_TIMEOUT = 6,       /* a bounded device-side wait ran out (persistent kernels)            */
   PM_DISCONNECTED = 7,  /* the ocean has more than one connected component                    */
-  PM_EBUSY = 8          /* no free server slot; retry after a pm_server_poll frees one         */
+  PM_EBUSY = 8,         /* no free server slot; retry after a pm_server_poll frees one         */
+  PM_EBOUNDS = 9        /* checked build only: a kernel read a bad neighbour index (skipped)   */
 };
 
 /* Lateral outer walls that are artificial slip boundaries Gamma_1 (Section 2, Eq. prim_bot_1:
@@ -387,6 +388,23 @@ enum { PM_KT_SPMV = 0,    /* SpMV + (p, Ap) reduction, one launch per PCG iterat
        PM_KT_COUNT = 5 };
 int pm_kernel_timing(int32_t enable);
 int pm_kernel_timing_get(int32_t kind, double* total_ms, int64_t* launches);
+
+/* Per-solve JSON log. With a path, every solved system appends one line to that file (opened in
+ * append mode): the entry point ("pcg_solve", "pcg_solve_noalloc", "project_step",
+ * "batch_solve", "server_solve"), rows, system, preconditioner, precision, status, iterations
+ * (total, outer, first pass), true and floor relative residuals, seconds, algorithmic bytes, GB/s,
+ * and, when hbm_peak_gbs > 0, GB/s as a percentage of it. NULL closes the log. Process-global,
+ * lines written under a lock. Errors: PM_EINVAL (the file cannot be opened; logging is then off).
+ * The library also marks its assemblies, solves, steps and their stages as NVTX ranges, which
+ * profilers show on their timelines. */
+int pm_set_log(const char* path, double hbm_peak_gbs);
+
+/* Build flags: PM_BUILD_CHECKED when the library was compiled with device index checks
+ * (PM_CHECKED). In that build every neighbour-column index a kernel reads is checked against the
+ * column count; a bad one is recorded and skipped (read as "no neighbour"), nothing faults, and
+ * the entry point that launched the kernel returns PM_EBOUNDS with the value in pm_last_error. */
+enum { PM_BUILD_CHECKED = 1 };
+int32_t pm_build_flags(void);
 
 #ifdef __cplusplus
 }

@@ -17,7 +17,9 @@ from . import build as _build
 
 # ---- C structures -----------------------------------------------------------------------------
 
-PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_NOT_CONVERGED, PM_BREAKDOWN, PM_TIMEOUT, PM_DISCONNECTED, PM_EBUSY = range(9)
+PM_OK, PM_EINVAL, PM_ENOMEM, PM_ECUDA, PM_NOT_CONVERGED, PM_BREAKDOWN, PM_TIMEOUT, PM_DISCONNECTED, PM_EBUSY, \
+    PM_EBOUNDS = range(10)
+PM_BUILD_CHECKED = 1
 PM_WALL_WEST, PM_WALL_EAST, PM_WALL_SOUTH, PM_WALL_NORTH = 1, 2, 4, 8
 OP_VEL_U1, OP_VEL_U2, OP_VEL_U3, OP_PRESSURE, OP_MASS = 0, 1, 2, 3, 4
 OP_VEL1_U1, OP_VEL1_U2, OP_VEL1_U3, OP_GRAD_X, OP_GRAD_Y, OP_GRAD_Z = 5, 6, 7, 8, 9, 10
@@ -119,6 +121,8 @@ SIGNATURES = {
     "pm_server_destroy": (None, [_P]),
     "pm_kernel_timing": (_I, [ctypes.c_int32]),
     "pm_kernel_timing_get": (_I, [ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]),
+    "pm_set_log": (_I, [ctypes.c_char_p, ctypes.c_double]),
+    "pm_build_flags": (ctypes.c_int32, []),
 }
 
 KT_SPMV, KT_UPDATE, KT_PUPDATE, KT_IC0, KT_LINE = 0, 1, 2, 3, 4
@@ -135,10 +139,31 @@ def kernel_timing_get(kind: int):
     return ms.value, cnt.value
 
 _lib = None
+_lib_path = _build.LIB
 
 
 def library_path() -> str:
     return _build.LIB
+
+
+def select_library(path: Optional[str] = None) -> str:
+    """Make every wrapper of this module call the library at `path` (None: the default build),
+    e.g. the checked build (build(checked=True)); returns the path selected before, to restore it.
+    Handles created through one library must not be passed to another."""
+    global _lib, _lib_path
+    prev = _lib_path
+    lib = load(path or _build.LIB)
+    _lib, _lib_path = lib, path or _build.LIB
+    return prev
+
+
+def set_log(path: Optional[str] = None, hbm_peak_gbs: float = 0.0):
+    """pm_set_log: append one JSON line per solved system to `path` (None closes the log)."""
+    _check(load().pm_set_log(os.fsencode(path) if path is not None else None, float(hbm_peak_gbs)), "set_log")
+
+
+def build_flags() -> int:
+    return int(load().pm_build_flags())
 
 
 def load(path: Optional[str] = None):

@@ -11,8 +11,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpm_gb300.so")
+# The checked build (device index checks, PM_CHECKED): a separate library for debugging and tests.
+OUT_DIR_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(OUT_DIR_CHECKED, "libpm_gb300_checked.so")
 SOURCES = ["pm_api.cu", "pm_mesh.cu", "pm_assemble.cu", "pm_solve.cu", "pm_step.cu", "pm_noalloc.cu",
-           "pm_batch.cu", "pm_checkpoint.cu"]
+           "pm_batch.cu", "pm_checkpoint.cu", "pm_trace.cu"]
 # The persistent batched kernel reads data other blocks write during the launch: plain global
 # loads in that file are cached in L2 only (ld.global.cg), never in the non-coherent L1.
 EXTRA = {"pm_batch.cu": ["-Xptxas", "-dlcm=cg"]}
@@ -31,9 +34,10 @@ def _flags():
                       "--expt-relaxed-constexpr", "-I", os.path.join(HERE, "..", "include")]
 
 
-def _compile(src: str, verbose_ptxas: bool) -> str:
-    obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc()] + _flags() + EXTRA.get(src, []) + ["-c", os.path.join(CSRC, src), "-o", obj]
+def _compile(src: str, verbose_ptxas: bool, checked: bool = False) -> str:
+    obj = os.path.join(OUT_DIR_CHECKED if checked else OUT_DIR, os.path.splitext(src)[0] + ".o")
+    cmd = [nvcc()] + _flags() + EXTRA.get(src, []) + (["-DPM_CHECKED"] if checked else []) + \
+        ["-c", os.path.join(CSRC, src), "-o", obj]
     if verbose_ptxas:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -44,28 +48,30 @@ def _compile(src: str, verbose_ptxas: bool) -> str:
     return obj
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(HERE, "..", "include", "pm.h"), __file__]
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
-def build(force: bool = False, verbose_ptxas: bool = False) -> str:
-    if not force and not _stale():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose_ptxas: bool = False, checked: bool = False) -> str:
+    """Compile and link the library (checked=True: the PM_CHECKED variant, its own directory)."""
+    lib = LIB_CHECKED if checked else LIB
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(OUT_DIR_CHECKED if checked else OUT_DIR, exist_ok=True)
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose_ptxas), SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, verbose_ptxas, checked), SOURCES))
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc()] + GENCODE + ["-shared", "-o", tmp] + objs + ["-lcudart_static", "-ldl", "-lrt", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv, checked="--checked" in sys.argv))

@@ -101,6 +101,7 @@ const char* pm_status_string(int s) {
     case PM_TIMEOUT: return "device wait timed out";
     case PM_DISCONNECTED: return "ocean is not connected";
     case PM_EBUSY: return "no free server slot";
+    case PM_EBOUNDS: return "bad index caught by a checked build";
   }
   return "unknown status";
 }
@@ -144,6 +145,7 @@ int64_t pm_operator_bytes(const pm_mesh_desc* d) {
 int pm_assemble_operator(const pm_mesh_desc* mesh, const pm_physics* phys, pm_operator** out,
                          pm_stream stream) {
   if (!mesh || !phys || !out) return set_error(PM_EINVAL, "null argument");
+  NvtxRange range("pm_assemble_operator");
   *out = nullptr;
   if (!(phys->dt > 0.0)) return set_error(PM_EINVAL, "dt must be > 0");
   for (int d = 0; d < 3; ++d)
@@ -212,6 +214,7 @@ int pm_assemble_operator(const pm_mesh_desc* mesh, const pm_physics* phys, pm_op
   for (int v = 0; v < VS_COUNT; ++v)
     PM_TRY(cuda_check(cudaMemsetAsync(op->d_val[v], 0, (size_t)NSLOT * op->npad * 8, s), "memset"));
   PM_TRY(launch_assemble(op, s));
+  PM_TRY(bounds_status("pm_assemble_operator"));
 #undef PM_TRY
   *out = op;
   return PM_OK;
@@ -287,13 +290,21 @@ int pm_spmv(pm_operator* op, pm_which which, const double* x, double* y, pm_stre
 int pm_residual(pm_operator* op, pm_which which, const double* b, const double* x, double* r, double* norms,
                 pm_stream stream) {
   if (!op || !b || !x || !r) return set_error(PM_EINVAL, "null argument");
-  return residual(op, (int)which, b, x, r, norms, (cudaStream_t)stream);
+  const int st = residual(op, (int)which, b, x, r, norms, (cudaStream_t)stream);
+  const int bs = bounds_status("pm_residual");
+  return bs ? bs : st;
 }
 
 int pm_pcg_solve(pm_operator* op, pm_which which, const double* b, double* x,
                  const pm_solve_opts* opts, pm_solve_stats* stats, pm_stream stream) {
   if (!op || !b || !x || !opts) return set_error(PM_EINVAL, "null argument");
-  return pcg_solve(op, (int)which, b, x, opts, stats, (cudaStream_t)stream);
+  pm_solve_stats local = {};
+  int r = pcg_solve(op, (int)which, b, x, opts, &local, (cudaStream_t)stream);
+  const int bs = bounds_status("pm_pcg_solve");
+  if (bs) r = bs;
+  if (stats) *stats = local;
+  if (log_enabled() && r != PM_EINVAL) log_solve("pcg_solve", op, (int)which, opts->prec, opts->precision, local);
+  return r;
 }
 
 int pm_state_create(pm_operator* op, pm_state** out) {
@@ -407,7 +418,21 @@ int pm_project_step(pm_operator* op, pm_state* st, const double* theta1, const d
   if (!op || !st || !vel || !pres || st->op != op) return set_error(PM_EINVAL, "bad argument");
   if (correction != PM_STEP_LUMPED && correction != PM_STEP_CONSISTENT)
     return set_error(PM_EINVAL, "unknown correction");
-  return project_step(op, st, theta1, theta2, vel, pres, correction, stats, (cudaStream_t)stream);
+  NvtxRange range("pm_project_step");
+  const int first = st->step == 0 ? PM_OP_VEL1_U1 : PM_OP_VEL_U1;
+  pm_solve_stats local[7] = {};
+  int r = project_step(op, st, theta1, theta2, vel, pres, correction, local, (cudaStream_t)stream);
+  const int bs = bounds_status("pm_project_step");
+  if (bs) r = bs;
+  if (stats)
+    for (int i = 0; i < 7; ++i) stats[i] = local[i];
+  if (log_enabled() && r != PM_EINVAL)
+    for (int i = 0; i < (correction == PM_STEP_CONSISTENT ? 7 : 4); ++i) {
+      const pm_solve_opts& o = i == 3 ? *pres : *vel;
+      const int w = i < 3 ? first + i : i == 3 ? PM_OP_PRESSURE : PM_OP_MASS;
+      log_solve("project_step", op, w, o.prec, o.precision, local[i]);
+    }
+  return r;
 }
 
 void pm_operator_destroy(pm_operator* op) { free_operator(op); }

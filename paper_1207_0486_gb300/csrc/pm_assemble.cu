@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(128) k_assemble(Geom g, double alpha, double n
     double hq[NNBR];
 #pragma unroll
     for (int q = 0; q < NNBR; ++q) {
-      const int nb = g.nbr[(int64_t)col * NNBR + q];
+      const int nb = nbr_of(g, col, q);
       hq[q] = nb >= 0 ? g.depth[nb] : 0.0;
     }
     const uint8_t cm = g.cellmask[col];
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(128) k_ic0_factor(Geom g, ColourMap cmap,
     const uint32_t smi = smask[row];
     int nbq[NNBR];
 #pragma unroll
-    for (int q = 0; q < NNBR; ++q) nbq[q] = g.nbr[(int64_t)col * NNBR + q];
+    for (int q = 0; q < NNBR; ++q) nbq[q] = nbr_of(g, col, q);
     double Lrow[NSLOT];
     double dsum = 0.0;
     // lower slots, visited in increasing neighbour colour
@@ -289,7 +289,7 @@ __global__ void k_keep_masks(Geom g, uint16_t* __restrict__ k0, uint16_t* __rest
     uint8_t fl[NNBR];
 #pragma unroll
     for (int q = 0; q < NNBR; ++q) {
-      nb[q] = q == 0 ? col : g.nbr[(int64_t)col * NNBR + q];
+      nb[q] = q == 0 ? col : nbr_of(g, col, q);
       fl[q] = nb[q] >= 0 ? g.colflag[nb[q]] : 0;
     }
     uint16_t* outs[3] = {k0, k1, k2};

@@ -168,7 +168,7 @@ __device__ __forceinline__ T row_spmv(const Geom& g, const T* __restrict__ val, 
   int nb[NNBR];
   nb[0] = col;
 #pragma unroll
-  for (int q = 1; q < NNBR; ++q) nb[q] = __ldg(g.nbr + col * NNBR + q);
+  for (int q = 1; q < NNBR; ++q) nb[q] = nbr_of(g, col, q);
   T a[NSLOT];
 #pragma unroll
   for (int s = 0; s < NSLOT; ++s) a[s] = __ldg(val + s * npad + row);
@@ -336,7 +336,7 @@ __device__ __forceinline__ T ic0_value(const Geom& g, int col, int k, int64_t pi
     const int kk = k + slot_dk(s);
     if (kk < 0 || kk >= nz) continue;
     const int q = slot_q(s);
-    const int nb = q == 0 ? col : __ldg(g.nbr + (int64_t)col * NNBR + q);
+    const int nb = q == 0 ? col : nbr_of(g, col, q);
     if (nb < 0) continue;
     acc = fma(-__ldg(F + (int64_t)s * g.n + pi), y[(int64_t)nb * nz + kk], acc);
   }
@@ -1339,6 +1339,7 @@ extern "C" int pm_batch_create(pm_operator* const* ops, const pm_which* which, c
 extern "C" int pm_batch_solve(pm_batch* bt, const double* const* b, double* const* x, pm_solve_stats* stats,
                               pm_stream stream) {
   if (!bt || !b || !x) return set_error(PM_EINVAL, "null argument");
+  NvtxRange range("pm_batch_solve " + std::to_string(bt->count) + " systems");
   auto t0 = std::chrono::steady_clock::now();
   cudaStream_t s = (cudaStream_t)stream;
   for (int i = 0; i < bt->count; ++i) {
@@ -1350,8 +1351,14 @@ extern "C" int pm_batch_solve(pm_batch* bt, const double* const* b, double* cons
   if (!st) st = batch::run_to_completion(bt, s, 64);
   if (st && st != PM_NOT_CONVERGED) return st;
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  const int fs = batch::finish(bt, stats, s, secs);
-  return st ? st : fs;
+  std::vector<pm_solve_stats> local(bt->count);
+  const int fs = batch::finish(bt, local.data(), s, secs);
+  if (stats) std::copy(local.begin(), local.end(), stats);
+  if (log_enabled())
+    for (int i = 0; i < bt->count; ++i)
+      log_solve("batch_solve", bt->ops[i], bt->which[i], bt->precs[i], bt->precision, local[i]);
+  const int bs = bounds_status("pm_batch_solve");
+  return bs ? bs : st ? st : fs;
 }
 
 extern "C" int pm_batch_info(const pm_batch* bt, int32_t* tile_cols, int32_t* block, int32_t* grid, int64_t* ntiles) {
@@ -1649,6 +1656,7 @@ extern "C" int pm_server_run(pm_server* sv, int32_t quantum, int32_t* active, pm
     sv->graph_tcap = sv->tcap;
     sv->graph_ic0 = ic0;
   }
+  NvtxRange range("pm_server_run");
   st = cuda_check(cudaGraphLaunch(sv->graph, s), "server graph launch");
   if (st) return st;
   count_launch();
@@ -1659,6 +1667,7 @@ extern "C" int pm_server_run(pm_server* sv, int32_t quantum, int32_t* active, pm
   if (!st) st = cuda_check(cudaStreamSynchronize(s), "server quantum");
   if (st) return st;
   if (sv->h_ctl[0].err) return set_error(sv->h_ctl[0].err, "server: a grid barrier wait expired");
+  if ((st = bounds_status("pm_server_run"))) return st;
   busy = 0;
   for (int i = 0; i < sv->cap; ++i) busy += sv->used[i] && sv->h_scal[i].state != ST_DONE;
   if (active) *active = busy;
@@ -1686,6 +1695,7 @@ extern "C" int pm_server_poll(pm_server* sv, int32_t* slots, pm_solve_stats* sta
       o.rel_residual_floor = c.rel_floor;
       const double nr = (double)sv->ops[i]->n;
       o.bytes_moved = c.iter * nr * (15 * es + 11 * es + 8 + 8) + c.outer * nr * (15 * 8 + 24);
+      if (log_enabled()) log_solve("server_solve", sv->ops[i], sv->which[i], sv->precs[i], sv->precision, o);
     }
     sv->used[i] = 0;
     sv->n_ic0 -= sv->precs[i] == PM_PREC_IC0;

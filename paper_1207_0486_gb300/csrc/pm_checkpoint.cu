@@ -109,6 +109,7 @@ extern "C" int pm_state_save(const pm_state* st, const char* path, pm_stream str
   using namespace pm;
   if (!st || !path) return set_error(PM_EINVAL, "null argument");
   if (!host_is_little_endian()) return set_error(PM_EINVAL, "checkpoint files are little-endian; this host is not");
+  NvtxRange range("pm_state_save");
   const pm_operator* op = st->op;
   cudaStream_t s = (cudaStream_t)stream;
   const std::string target(path);
@@ -149,6 +150,7 @@ extern "C" int pm_state_load(pm_state* st, const char* path, pm_stream stream) {
   using namespace pm;
   if (!st || !path) return set_error(PM_EINVAL, "null argument");
   if (!host_is_little_endian()) return set_error(PM_EINVAL, "checkpoint files are little-endian; this host is not");
+  NvtxRange range("pm_state_load");
   const pm_operator* op = st->op;
   cudaStream_t s = (cudaStream_t)stream;
   FILE* fh = std::fopen(path, "rb");

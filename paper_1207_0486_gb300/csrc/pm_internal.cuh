@@ -16,6 +16,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -24,6 +25,65 @@
 #include "../../include/pm.h"
 
 namespace pm {
+
+// Host-side NVTX range for the lifetime of a scope: profilers show the library's assemblies,
+// solves, steps and their stages on the timeline. Without a profiler attached the calls return
+// at once.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  explicit NvtxRange(const std::string& name) { nvtxRangePushA(name.c_str()); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// ---- checked build (PM_CHECKED): device-side index checks --------------------------------------
+// Every neighbour-column index a kernel reads is checked against the column count; the first bad
+// one is recorded (site, value, limit) and read as "no neighbour", so the kernel skips the access
+// instead of faulting, and the entry point that launched it returns PM_EBOUNDS. Each translation
+// unit has its own record (no relocatable device code) and registers a reader for it at load time.
+enum BoundsSite { SITE_NONE = 0, SITE_NBR = 1 };
+struct BoundsRecord {
+  int32_t flag, site;
+  int64_t value, limit;
+};
+using BoundsReader = int (*)(BoundsRecord*);
+void register_bounds_reader(BoundsReader r);   // pm_trace.cu
+// PM_EBOUNDS with a message when a checked kernel recorded a bad index since the last call
+// (clears the records); PM_OK otherwise, and always in an unchecked build.
+int bounds_status(const char* where);
+#ifdef PM_CHECKED
+namespace {
+__device__ BoundsRecord g_bounds_tu;
+__device__ __noinline__ void record_bad_index(int site, int64_t value, int64_t limit) {
+  if (atomicCAS(&g_bounds_tu.flag, 0, 1) == 0) {
+    g_bounds_tu.site = site;
+    g_bounds_tu.value = value;
+    g_bounds_tu.limit = limit;
+  }
+}
+int read_bounds_tu(BoundsRecord* out) {
+  if (cudaMemcpyFromSymbol(out, g_bounds_tu, sizeof(BoundsRecord)) != cudaSuccess) return 0;
+  if (out->flag) {
+    const BoundsRecord zero = {0, 0, 0, 0};
+    cudaMemcpyToSymbol(g_bounds_tu, &zero, sizeof(BoundsRecord));
+  }
+  return out->flag;
+}
+struct BoundsRegistration {
+  BoundsRegistration() { register_bounds_reader(&read_bounds_tu); }
+} g_bounds_registration_tu;
+}  // namespace
+#endif
+
+// ---- per-solve JSON log (pm_set_log) -------------------------------------------------------------
+const char* which_name(int which);
+const char* prec_name(int prec);
+const char* precision_name(int precision);
+bool log_enabled();
+// One JSON line for one solved system: event name, basin size, system, options and its stats.
+void log_solve(const char* event, const pm_operator* op, int which, int prec, int precision,
+               const pm_solve_stats& st);
 
 constexpr int NSLOT = 15;
 constexpr int NNBR = 7;
@@ -145,6 +205,18 @@ struct Geom {
   const double* coriolis;   // [ncols] or null
 };
 
+// Neighbour column q of column col (-1: none; q = 0 is col itself). Checked builds validate it.
+__device__ __forceinline__ int nbr_of(const Geom& g, int64_t col, int q) {
+  const int nb = __ldg(g.nbr + col * NNBR + q);
+#ifdef PM_CHECKED
+  if (nb < -1 || nb >= g.ncols) {
+    record_bad_index(SITE_NBR, nb, g.ncols);
+    return -1;
+  }
+#endif
+  return nb;
+}
+
 // r_i = b_i - (A x)_i for one row of the column-sliced operator, by Dot2 (Ogita, Rump & Oishi):
 // every product a_ij x_j is split exactly into p + e (two_product), the -p are summed into b_i by
 // two_sum, and both rounding errors are accumulated and added once at the end. The result is as
@@ -163,7 +235,7 @@ __device__ __forceinline__ double row_residual_dot2(const Geom& g, const double*
   uint8_t fl[NNBR];
   nb[0] = col;
 #pragma unroll
-  for (int q = 1; q < NNBR; ++q) nb[q] = __ldg(g.nbr + col * NNBR + q);
+  for (int q = 1; q < NNBR; ++q) nb[q] = nbr_of(g, col, q);
   if (MASKC >= 0) {
 #pragma unroll
     for (int q = 0; q < NNBR; ++q) fl[q] = __ldg(g.colflag + (nb[q] >= 0 ? nb[q] : col));

@@ -119,7 +119,7 @@ __device__ __forceinline__ double row_dot(const Geom& g, const double* __restric
   uint8_t fl[NNBR];
 #pragma unroll
   for (int q = 0; q < NNBR; ++q) {
-    nb[q] = q == 0 ? col : g.nbr[(int64_t)col * NNBR + q];
+    nb[q] = q == 0 ? col : nbr_of(g, col, q);
     if (MASKC >= 0) fl[q] = nb[q] >= 0 ? g.colflag[nb[q]] : 0;
   }
   double sum = 0.0;
@@ -487,10 +487,17 @@ extern "C" int pm_pcg_solve_noalloc(pm_operator* op, pm_which which, const doubl
   v.dinv = base + na::OFF_DINV;
   v.part = base + na::OFF_PART;
   v.sc = reinterpret_cast<PcgScalars*>(base + na::OFF_SC);
+  NvtxRange range(std::string("pcg_noalloc ") + which_name((int)which) + " " + prec_name(opts->prec));
+  pm_solve_stats local = {};
   switch (which_mask((int)which)) {
-    case 0: return na::run<0>(op, (int)which, b, x, opts, stats, s, v);
-    case 1: return na::run<1>(op, (int)which, b, x, opts, stats, s, v);
-    case 2: return na::run<2>(op, (int)which, b, x, opts, stats, s, v);
-    default: return na::run<-1>(op, (int)which, b, x, opts, stats, s, v);
+    case 0: st = na::run<0>(op, (int)which, b, x, opts, &local, s, v); break;
+    case 1: st = na::run<1>(op, (int)which, b, x, opts, &local, s, v); break;
+    case 2: st = na::run<2>(op, (int)which, b, x, opts, &local, s, v); break;
+    default: st = na::run<-1>(op, (int)which, b, x, opts, &local, s, v); break;
   }
+  const int bs = bounds_status("pm_pcg_solve_noalloc");
+  if (bs) st = bs;
+  if (stats) *stats = local;
+  if (log_enabled()) log_solve("pcg_solve_noalloc", op, (int)which, opts->prec, PM_FP64, local);
+  return st;
 }

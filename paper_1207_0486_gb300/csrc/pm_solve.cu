@@ -187,7 +187,7 @@ __device__ __forceinline__ double row_dot(const Geom& g, const TV* __restrict__ 
   uint8_t fl[NNBR];
   nb[0] = col;
 #pragma unroll
-  for (int q = 1; q < NNBR; ++q) nb[q] = __ldg(g.nbr + col * NNBR + q);
+  for (int q = 1; q < NNBR; ++q) nb[q] = nbr_of(g, col, q);
   if (MASKC >= 0) {
 #pragma unroll
     for (int q = 0; q < NNBR; ++q) fl[q] = __ldg(g.colflag + (nb[q] >= 0 ? nb[q] : col));
@@ -228,7 +228,7 @@ __device__ __forceinline__ double row_dot_keep(const Geom& g, const TV* __restri
   int nb[NNBR];
   nb[0] = col;
 #pragma unroll
-  for (int q = 1; q < NNBR; ++q) nb[q] = __ldg(g.nbr + col * NNBR + q);
+  for (int q = 1; q < NNBR; ++q) nb[q] = nbr_of(g, col, q);
   TV a[NSLOT];
 #pragma unroll
   for (int s = 0; s < NSLOT; ++s) a[s] = __ldg(val + s * npad + row);
@@ -483,7 +483,7 @@ __device__ __forceinline__ void ic0_row(const Geom& g, const CMap& cm, const int
     const int q = slot_q(s);
     const int kk = k + slot_dk(s);
     if (kk < 0 || kk >= nz) continue;
-    const int nb = q == 0 ? col : __ldg(g.nbr + (int64_t)col * NNBR + q);
+    const int nb = q == 0 ? col : nbr_of(g, col, q);
     if (nb < 0) continue;
     acc = fma(-F[(int64_t)s * g.n + pi], y[(int64_t)nb * nz + kk], acc);
   }
@@ -1655,7 +1655,7 @@ __device__ __forceinline__ float row_dot32(const Geom& g, const TV* __restrict__
   uint8_t fl[NNBR];
   nb[0] = col;
 #pragma unroll
-  for (int q = 1; q < NNBR; ++q) nb[q] = __ldg(g.nbr + col * NNBR + q);
+  for (int q = 1; q < NNBR; ++q) nb[q] = nbr_of(g, col, q);
   if (MASKC >= 0) {
 #pragma unroll
     for (int q = 0; q < NNBR; ++q) fl[q] = __ldg(g.colflag + (nb[q] >= 0 ? nb[q] : col));
@@ -1698,7 +1698,7 @@ __device__ __forceinline__ float row_dot32_keep(const Geom& g, const TV* __restr
   int nb[NNBR];
   nb[0] = col;
 #pragma unroll
-  for (int q = 1; q < NNBR; ++q) nb[q] = __ldg(g.nbr + col * NNBR + q);
+  for (int q = 1; q < NNBR; ++q) nb[q] = nbr_of(g, col, q);
   float a[NSLOT];
 #pragma unroll
   for (int s = 0; s < NSLOT; ++s) a[s] = ldv(val, s * npad + row);
@@ -2189,7 +2189,7 @@ __global__ void __launch_bounds__(TPB) k32_ic0_sweep(Geom g, CMap cm, const int3
       const int q = slot_q(s);
       const int kk = k + slot_dk(s);
       if (kk < 0 || kk >= nz) continue;
-      const int nb = q == 0 ? col : __ldg(g.nbr + (int64_t)col * NNBR + q);
+      const int nb = q == 0 ? col : nbr_of(g, col, q);
       if (nb < 0) continue;
       acc = fmaf(-F[(int64_t)s * g.n + pi], y[(int64_t)nb * nz + kk], acc);
     }
@@ -2609,6 +2609,7 @@ int pcg_solve(pm_operator* op, int which, const double* b, double* x, const pm_s
   if (!(o->rtol > 0.0) || o->max_iter < 0) return set_error(PM_EINVAL, "rtol must be > 0, max_iter >= 0");
   if (o->precision < PM_FP64 || o->precision > PM_BF16_REFINE) return set_error(PM_EINVAL, "unknown precision");
   if (o->kernel < PM_KERNEL_AUTO || o->kernel > PM_KERNEL_RESIDENT) return set_error(PM_EINVAL, "unknown kernel choice");
+  NvtxRange range(std::string("pcg ") + which_name(which) + " " + prec_name(o->prec) + " " + precision_name(o->precision));
   int r = ensure_ctx(op);
   if (r) return r;
   if (o->precision == PM_FP32_REFINE) {

@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(TPB) k_rhs_vel(Geom g, StepIn in) {
     double hq[NNBR];
 #pragma unroll
     for (int q = 0; q < NNBR; ++q) {
-      nb[q] = g.nbr[(int64_t)col * NNBR + q];
+      nb[q] = nbr_of(g, col, q);
       hq[q] = nb[q] >= 0 ? g.depth[nb[q]] : 0.0;
     }
     const uint8_t cm = g.cellmask[col];
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(TPB) k_div_rhs(Geom g, GradIn in, double alpha
     const int k = (int)(row - (int64_t)col * nz);
     int nb[NNBR];
 #pragma unroll
-    for (int q = 0; q < NNBR; ++q) nb[q] = q == 0 ? col : g.nbr[(int64_t)col * NNBR + q];
+    for (int q = 0; q < NNBR; ++q) nb[q] = q == 0 ? col : nbr_of(g, col, q);
     double s = 0.0;
 #pragma unroll
     for (int sl = 0; sl < NSLOT; ++sl) {
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(TPB) k_correct(Geom g, GradIn in, const double
     const int k = (int)(row - (int64_t)col * nz);
     int nb[NNBR];
 #pragma unroll
-    for (int qq = 0; qq < NNBR; ++qq) nb[qq] = qq == 0 ? col : g.nbr[(int64_t)col * NNBR + qq];
+    for (int qq = 0; qq < NNBR; ++qq) nb[qq] = qq == 0 ? col : nbr_of(g, col, qq);
     double s[3] = {0, 0, 0};
 #pragma unroll
     for (int sl = 0; sl < NSLOT; ++sl) {
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(TPB) k_correct_rhs(Geom g, GradIn in, const do
     const int k = (int)(row - (int64_t)col * nz);
     int nb[NNBR];
 #pragma unroll
-    for (int qq = 0; qq < NNBR; ++qq) nb[qq] = qq == 0 ? col : g.nbr[(int64_t)col * NNBR + qq];
+    for (int qq = 0; qq < NNBR; ++qq) nb[qq] = qq == 0 ? col : nbr_of(g, col, qq);
     double s[3] = {0, 0, 0}, mu[3] = {0, 0, 0};
 #pragma unroll
     for (int sl = 0; sl < NSLOT; ++sl) {
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(TPB) k_diagnostics(Geom g, const double* __res
     const int k = (int)(row - (int64_t)col * nz);
     int nb[NNBR];
 #pragma unroll
-    for (int q = 0; q < NNBR; ++q) nb[q] = q == 0 ? col : g.nbr[(int64_t)col * NNBR + q];
+    for (int q = 0; q < NNBR; ++q) nb[q] = q == 0 ? col : nbr_of(g, col, q);
     double mu[3] = {0, 0, 0}, du = 0.0, dut = 0.0;
 #pragma unroll
     for (int sl = 0; sl < NSLOT; ++sl) {
@@ -415,8 +415,11 @@ int project_step(pm_operator* op, pm_state* st, const double* th1, const double*
   in.th[1] = th2;
   in.inv_dt = 1.0 / op->dt;
   in.bdf1 = bdf1 ? 1 : 0;
-  k_rhs_vel<<<G, TPB, 0, s>>>(g, in);
-  count_launch();
+  {
+    NvtxRange range("velocity right-hand sides");
+    k_rhs_vel<<<G, TPB, 0, s>>>(g, in);
+    count_launch();
+  }
   int st_all = PM_OK;
   pm_solve_stats local[7];
   for (int i = 0; i < 7; ++i) local[i] = pm_solve_stats{};
@@ -435,8 +438,11 @@ int project_step(pm_operator* op, pm_state* st, const double* th1, const double*
     gi.u[c] = st->ut[c];
     gi.out[c] = st->u_prev[c];  // u^{k-1} is no longer needed: it receives u^{k+1}
   }
-  k_div_rhs<<<G, TPB, 0, s>>>(g, gi, alpha, st->bp);
-  count_launch();
+  {
+    NvtxRange range("divergence right-hand side");
+    k_div_rhs<<<G, TPB, 0, s>>>(g, gi, alpha, st->bp);
+    count_launch();
+  }
   {
     pm_solve_opts o = *pres;
     o.x0_is_guess = 1;
@@ -446,6 +452,7 @@ int project_step(pm_operator* op, pm_state* st, const double* th1, const double*
   }
   k_axpy<<<G, TPB, 0, s>>>(op->n, 1.0, st->q, st->p);
   count_launch();
+  NvtxRange correction_range(correction == PM_STEP_CONSISTENT ? "consistent-mass correction" : "lumped correction");
   if (correction == PM_STEP_CONSISTENT) {
     // b[c] <- M u~_c - G_c q / alpha, then M u_c = b[c] by PCG with x0 = u~_c
     GradIn gr = gi;

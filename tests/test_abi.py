@@ -142,3 +142,17 @@ def test_server_and_batch_validation_without_gpu(lib_path):
     assert lib.pm_batch_solve(None, None, None, None, None) == api.PM_EINVAL
     assert lib.pm_batch_info(None, None, None, None, None) == api.PM_EINVAL
     lib.pm_batch_destroy(None)
+
+
+def test_log_file_and_build_flags_without_gpu(lib_path, tmp_path):
+    """pm_set_log opens (append) and closes the per-solve log on the host; an unopenable path is
+    PM_EINVAL and leaves logging off. The default build is not the checked one."""
+    import paper_1207_0486_gb300.api as api
+    lib = api.load()
+    path = tmp_path / "solves.jsonl"
+    assert lib.pm_set_log(str(path).encode(), 6800.0) == api.PM_OK
+    assert path.exists() and path.read_text() == ""
+    assert lib.pm_set_log(None, 0.0) == api.PM_OK
+    assert lib.pm_set_log(str(tmp_path / "missing" / "x.jsonl").encode(), 0.0) == api.PM_EINVAL
+    assert lib.pm_build_flags() == 0
+    assert lib.pm_status_string(api.PM_EBOUNDS) == b"bad index caught by a checked build"
