@@ -411,6 +411,21 @@ def run_batched_leg(dist, world, rank):
     nsys = _gather_sum(dist, len(sys_ops))
     nodes = _gather_sum(dist, sum(op.n for op in ops))
     bad = _gather_sum(dist, sum(1 for s in stats if s.status != pm.PM_OK))
+    # the same batch with BF16 operator values (FP32 vectors, FP64 refinement), autotuned too
+    bf = pm.Batch(sys_ops, sys_w, pm.Options(rtol=1e-8, prec=pm.PREC_LINE, precision=pm.BF16_REFINE,
+                                             inner_rtol=1e-4, max_iter=200000), autotune=True)
+    bf.solve(bs, xs, allow_not_converged=True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    bf_stats = bf.solve(bs, xs, allow_not_converged=True)
+    torch.cuda.synchronize()
+    t_bf = _gather_max(dist, time.perf_counter() - t0)
+    bf.close()
+    bf16 = {"batched_s": round(t_bf, 3), "solves_per_s": round(nsys / t_bf, 2),
+            "speedup_vs_sequential_fp64": round(t_seq / t_bf, 3), "iters_max": max(int(s.iters) for s in bf_stats),
+            "failed": int(_gather_sum(dist, sum(1 for s in bf_stats if s.status != pm.PM_OK)))}
     mass = _consistent_mass_batch(dist, ops, gen)
     for op in ops:
         op.close()
@@ -421,7 +436,7 @@ def run_batched_leg(dist, world, rank):
             "solves_per_s": round(nsys / t_batch, 2), "sequential_solves_per_s": round(nsys / t_seq, 2),
             "speedup_vs_sequential_fp64": round(t_seq / t_batch, 3), "failed": int(bad),
             "iters_max": max(int(s.iters) for s in stats), "sequential_iters_max": max(int(s.iters) for s in sst),
-            "autotuned": info, "consistent_mass_ic0": mass}
+            "autotuned": info, "bf16_refine": bf16, "consistent_mass_ic0": mass}
 
 
 def _consistent_mass_batch(dist, ops, gen):

@@ -230,8 +230,9 @@ int pm_pcg_solve_noalloc(pm_operator* op, pm_which which, const double* b, doubl
  * step's IC0 velocity and mass systems next to line-preconditioned pressure systems. IC0 applies
  * the same multicolour factor as the single-system solve: its 16 colour sweeps run as 16 phases of
  * the persistent kernel with a grid barrier after each, so a batch holding an IC0 system waits at
- * 22 grid barriers per iteration instead of 5. Precision: PM_FP64, or PM_FP32_REFINE (FP32
- * difference-form values and vectors, FP64 x, dots and true-residual restarts). Starts from x = 0;
+ * 22 grid barriers per iteration instead of 5. Precision: PM_FP64, PM_FP32_REFINE (FP32
+ * difference-form values and vectors, FP64 x, dots and true-residual restarts), or
+ * PM_BF16_REFINE (the same with BF16 difference-form values: FP32 vectors and factors). Starts from x = 0;
  * the pressure zero-mean reading applies to PM_OP_PRESSURE entries. autotune != 0 times the tile
  * width (columns per tile: 16, 32, 64) x block size (128, 256) on this batch once and caches the
  * choice per size bucket. Grid waits are bounded: an expired wait returns PM_TIMEOUT. The batch
@@ -265,8 +266,9 @@ int pm_pcg_solve_batched(pm_operator* const* ops, const pm_which* which, const d
  * drain; each system's iterates depend on nothing but its own tiles (bit-identical whatever else
  * is resident, for a fixed tile_cols and block). No paper counterpart: the paper solves one basin;
  * this serves many basins' PCG solves (Section 5) at once.
- * opts: as pm_batch_create (PM_PREC_JACOBI / PM_PREC_LINE / PM_PREC_IC0 / PM_PREC_NONE; PM_FP64
- * or PM_FP32_REFINE); every system uses them unless its admission names its own preconditioner. nz_cap: the largest nz admitted (sizes shared memory).
+ * opts: as pm_batch_create (PM_PREC_JACOBI / PM_PREC_LINE / PM_PREC_IC0 / PM_PREC_NONE; PM_FP64,
+ * PM_FP32_REFINE or PM_BF16_REFINE); every system uses them unless its admission names its own
+ * preconditioner. nz_cap: the largest nz admitted (sizes shared memory).
  * tile_cols: 16, 32 or 64 columns per tile; block: 128 or 256 threads; blocks_per_sm: resident
  * blocks per SM of the kernel (0 = as many as fit). Errors: PM_EINVAL, PM_ENOMEM, PM_ECUDA. */
 int pm_server_create(int32_t slots, int32_t nz_cap, const pm_solve_opts* opts, int32_t tile_cols,

@@ -64,6 +64,7 @@ struct Sys {
   int32_t maskc, proj, prec;
   int32_t tile0, ntiles;  // the system's tiles [tile0, tile0 + ntiles) (partials, block ownership)
   int32_t tw;             // columns per tile (the last tile may have fewer)
+  int32_t vbf16;          // FP32 system whose operator values are BF16 (difference form)
 };
 
 struct Scal {
@@ -156,12 +157,18 @@ __device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
 template <typename T>
 __device__ __forceinline__ T ldv(const T* p, int i) { return __ldg(p + i); }
 
+__device__ __forceinline__ double ldval(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float ldval(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float ldval(const __nv_bfloat16* p) {
+  return __bfloat162float(__ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short*>(p))));
+}
+
 // Row of A for phase A. MASKC: velocity component whose Dirichlet rows are identity rows (0, 1, 2;
 // a compile-time constant so the per-slot tests fold), or -1 (pressure: none). The slot values are
 // loaded before the neighbour indices are used, and the iterate with plain loads: this file is
 // compiled with L2-only default loads, and the iterate is written only in other phases.
-template <typename T, int MASKC>
-__device__ __forceinline__ T row_spmv(const Geom& g, const T* __restrict__ val, const T* x, int row, int col,
+template <typename T, int MASKC, typename V = T>
+__device__ __forceinline__ T row_spmv(const Geom& g, const V* __restrict__ val, const T* x, int row, int col,
                                            int k) {
   constexpr bool MASK = MASKC >= 0;
   const int nz = g.nz, npad = (int)g.npad;
@@ -171,7 +178,7 @@ __device__ __forceinline__ T row_spmv(const Geom& g, const T* __restrict__ val, 
   for (int q = 1; q < NNBR; ++q) nb[q] = nbr_of(g, col, q);
   T a[NSLOT];
 #pragma unroll
-  for (int s = 0; s < NSLOT; ++s) a[s] = __ldg(val + s * npad + row);
+  for (int s = 0; s < NSLOT; ++s) a[s] = ldval(val + s * npad + row);
   uint8_t fl[NNBR];
   if (MASK) {
 #pragma unroll
@@ -214,11 +221,11 @@ __device__ __forceinline__ T row_spmv(const Geom& g, const T* __restrict__ val, 
 
 // Phase A of one tile: w = A p on its rows, returns the partial (p, w). Two rows per thread are
 // computed before either is stored.
-template <typename T, int MASKC>
+template <typename T, int MASKC, typename V = T>
 __device__ __forceinline__ double spmv_tile(const Sys& S, int row0, int rows, int nz) {
   const T* p = (const T*)S.p;
   T* w = (T*)S.w;
-  const T* val = (const T*)S.val;
+  const V* val = (const V*)S.val;
   const Geom g = S.g;
   const int bd = blockDim.x;
   AccFor<T> acc;   // FP64 for FP64 systems, compensated FP32 for FP32 ones
@@ -228,7 +235,7 @@ __device__ __forceinline__ double spmv_tile(const Sys& S, int row0, int rows, in
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
       const int row = row0 + min(i0 + u * bd, rows - 1), col = row / nz, k = row - col * nz;
-      wv[u] = row_spmv<T, MASKC>(g, val, p, row, col, k);
+      wv[u] = row_spmv<T, MASKC, V>(g, val, p, row, col, k);
       pv[u] = p[row];
     }
 #pragma unroll
@@ -632,11 +639,20 @@ __global__ void __launch_bounds__(256, PM_BATCH_MINB) k_batch(const Sys* __restr
       const int nz = S.g.nz, row0 = tl.col0 * nz, rows = tl.ncols * nz;
       double v[NP] = {0.0, 0.0, 0.0, 0.0};
       if (state == ST_ITER) {
-        switch (S.maskc) {
-          case 0: v[0] = spmv_tile<T, 0>(S, row0, rows, nz); break;
-          case 1: v[0] = spmv_tile<T, 1>(S, row0, rows, nz); break;
-          case 2: v[0] = spmv_tile<T, 2>(S, row0, rows, nz); break;
-          default: v[0] = spmv_tile<T, -1>(S, row0, rows, nz); break;
+        if (std::is_same<T, float>::value && S.vbf16) {
+          switch (S.maskc) {
+            case 0: v[0] = spmv_tile<T, 0, __nv_bfloat16>(S, row0, rows, nz); break;
+            case 1: v[0] = spmv_tile<T, 1, __nv_bfloat16>(S, row0, rows, nz); break;
+            case 2: v[0] = spmv_tile<T, 2, __nv_bfloat16>(S, row0, rows, nz); break;
+            default: v[0] = spmv_tile<T, -1, __nv_bfloat16>(S, row0, rows, nz); break;
+          }
+        } else {
+          switch (S.maskc) {
+            case 0: v[0] = spmv_tile<T, 0>(S, row0, rows, nz); break;
+            case 1: v[0] = spmv_tile<T, 1>(S, row0, rows, nz); break;
+            case 2: v[0] = spmv_tile<T, 2>(S, row0, rows, nz); break;
+            default: v[0] = spmv_tile<T, -1>(S, row0, rows, nz); break;
+          }
         }
       } else if (state == ST_REFINE) {
         switch (S.maskc) {
@@ -981,11 +997,15 @@ size_t smem_bytes(const pm_batch* bt) {
 // Descriptor of one system: operator values (FP64, or the FP32 difference form), Jacobi
 // diagonal, the preconditioner's factors (line: Thomas factors; IC0: factor, column-class index,
 // grid parities, colour bases, level counts), mass vector. Vectors and tiles are set by the caller.
-void fill_sys(Sys* S, pm_operator* op, int w, int prec, bool f32) {
+void fill_sys(Sys* S, pm_operator* op, int w, int prec, int precision) {
   const int vs = which_valset(w);
+  const bool f32 = precision != PM_FP64;
   *S = Sys{};
   S->g = geom_of(op);
-  S->val = f32 ? (const void*)op->d_val32[vs] : (const void*)op->d_val[vs];
+  S->val = precision == PM_BF16_REFINE ? (const void*)op->d_val16[vs]
+           : f32                       ? (const void*)op->d_val32[vs]
+                                       : (const void*)op->d_val[vs];
+  S->vbf16 = precision == PM_BF16_REFINE ? 1 : 0;
   S->val64 = op->d_val[vs];
   S->dinv = f32 ? (const void*)op->d_dinv32[w] : (const void*)op->d_dinv[w];
   S->lineF = prec == PM_PREC_LINE ? (f32 ? (const void*)op->d_line32[w] : (const void*)op->d_line[w]) : nullptr;
@@ -1059,7 +1079,7 @@ int build_layout(pm_batch* bt) {
   for (int s = 0; s < bt->count; ++s) {
     pm_operator* op = bt->ops[s];
     Sys& S = bt->hsys[s];
-    fill_sys(&S, op, bt->which[s], bt->precs[s], f32);
+    fill_sys(&S, op, bt->which[s], bt->precs[s], bt->precision);
     S.r = take(op->n * es);
     S.p = take(op->n * es);
     S.w = take(op->n * es);
@@ -1185,7 +1205,8 @@ int finish(pm_batch* bt, pm_solve_stats* stats, cudaStream_t s, double seconds) 
   if (!st) st = cuda_check(cudaStreamSynchronize(s), "batched PCG finish");
   if (st) return st;
   int worst = PM_OK;
-  const double es = bt->precision == PM_FP64 ? 8.0 : 4.0;
+  const double es = bt->precision == PM_FP64 ? 8.0 : 4.0;                    // vector bytes
+  const double vb = bt->precision == PM_FP64 ? 8.0 : bt->precision == PM_FP32_REFINE ? 4.0 : 2.0;  // values
   for (int i = 0; i < bt->count; ++i) {
     const Scal& c = hs[i];
     if (c.status != PM_OK && worst == PM_OK) worst = c.status;
@@ -1200,7 +1221,7 @@ int finish(pm_batch* bt, pm_solve_stats* stats, cudaStream_t s, double seconds) 
       o.rel_residual_floor = c.rel_floor;
       o.seconds = seconds;
       const double n = (double)bt->ops[i]->n;
-      o.bytes_moved = c.iter * n * (15 * es + 11 * es + 8 + 8) + c.outer * n * (15 * 8 + 24);
+      o.bytes_moved = c.iter * n * (15 * vb + 11 * es + 8 + 8) + c.outer * n * (15 * 8 + 24);
     }
   }
   if (worst != PM_OK) return set_error(worst, "batched PCG: some systems did not converge");
@@ -1295,8 +1316,8 @@ extern "C" int pm_batch_create(pm_operator* const* ops, const pm_which* which, c
   for (int i = 0; prec && i < count; ++i)
     if (prec[i] != PM_PREC_DEFAULT && !batch::known_prec(prec[i]))
       return set_error(PM_EINVAL, "unknown preconditioner in the per-entry list");
-  if (opts->precision != PM_FP64 && opts->precision != PM_FP32_REFINE)
-    return set_error(PM_EINVAL, "batched PCG supports PM_FP64 and PM_FP32_REFINE");
+  if (opts->precision != PM_FP64 && opts->precision != PM_FP32_REFINE && opts->precision != PM_BF16_REFINE)
+    return set_error(PM_EINVAL, "unknown precision");
   if (!(opts->rtol > 0.0)) return set_error(PM_EINVAL, "rtol must be > 0");
   cudaStream_t s = (cudaStream_t)stream;
   pm_batch* bt = new pm_batch();
@@ -1494,8 +1515,8 @@ extern "C" int pm_server_create(int32_t slots, int32_t nz_cap, const pm_solve_op
     return set_error(PM_EINVAL, "bad server arguments");
   *out = nullptr;
   if (!known_prec(opts->prec)) return set_error(PM_EINVAL, "unknown preconditioner");
-  if (opts->precision != PM_FP64 && opts->precision != PM_FP32_REFINE)
-    return set_error(PM_EINVAL, "server supports PM_FP64 and PM_FP32_REFINE");
+  if (opts->precision != PM_FP64 && opts->precision != PM_FP32_REFINE && opts->precision != PM_BF16_REFINE)
+    return set_error(PM_EINVAL, "unknown precision");
   if (!(opts->rtol > 0.0)) return set_error(PM_EINVAL, "rtol must be > 0");
   if (tile_cols != 16 && tile_cols != 32 && tile_cols != 64) return set_error(PM_EINVAL, "tile_cols must be 16, 32 or 64");
   if ((block != 128 && block != 256) || tile_cols > block) return set_error(PM_EINVAL, "block must be 128 or 256");
@@ -1590,7 +1611,7 @@ extern "C" int pm_server_admit(pm_server* sv, pm_operator* op, pm_which which, i
     return p;
   };
   Sys& S = sv->hsys[s_i];
-  fill_sys(&S, op, (int)which, pi, f32);
+  fill_sys(&S, op, (int)which, pi, sv->precision);
   S.r = take(op->n * es);
   S.p = take(op->n * es);
   S.w = take(op->n * es);
@@ -1678,7 +1699,8 @@ extern "C" int pm_server_poll(pm_server* sv, int32_t* slots, pm_solve_stats* sta
   using namespace pm::batch;
   if (!sv || !slots || !n_out || max_out < 0) return set_error(PM_EINVAL, "bad server poll arguments");
   int n = 0;
-  const double es = sv->precision == PM_FP64 ? 8.0 : 4.0;
+  const double es = sv->precision == PM_FP64 ? 8.0 : 4.0;                    // vector bytes
+  const double vb = sv->precision == PM_FP64 ? 8.0 : sv->precision == PM_FP32_REFINE ? 4.0 : 2.0;  // values
   for (int i = 0; i < sv->cap && n < max_out; ++i) {
     if (!sv->used[i] || sv->h_scal[i].state != ST_DONE) continue;
     const Scal& c = sv->h_scal[i];
@@ -1694,7 +1716,7 @@ extern "C" int pm_server_poll(pm_server* sv, int32_t* slots, pm_solve_stats* sta
       o.rel_residual_rec = c.bb > 0 ? std::sqrt(c.rr / c.bb) : 0.0;
       o.rel_residual_floor = c.rel_floor;
       const double nr = (double)sv->ops[i]->n;
-      o.bytes_moved = c.iter * nr * (15 * es + 11 * es + 8 + 8) + c.outer * nr * (15 * 8 + 24);
+      o.bytes_moved = c.iter * nr * (15 * vb + 11 * es + 8 + 8) + c.outer * nr * (15 * 8 + 24);
       if (log_enabled()) log_solve("server_solve", sv->ops[i], sv->which[i], sv->precs[i], sv->precision, o);
     }
     sv->used[i] = 0;

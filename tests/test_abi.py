@@ -116,7 +116,7 @@ def test_server_and_batch_validation_without_gpu(lib_path):
         a = {**good, **b}
         assert lib.pm_server_create(a["slots"], a["nz_cap"], opts(), a["tile_cols"], a["block"], a["bps"],
                                     ctypes.byref(out), None) == api.PM_EINVAL, b
-    for o in (opts(prec=7), opts(prec=-1), opts(precision=api.BF16_REFINE), opts(rtol=0.0)):
+    for o in (opts(prec=7), opts(prec=-1), opts(precision=3), opts(rtol=0.0)):
         assert lib.pm_server_create(8, 32, o, 64, 128, 0, ctypes.byref(out), None) == api.PM_EINVAL
     assert lib.pm_server_create(8, 32, None, 64, 128, 0, ctypes.byref(out), None) == api.PM_EINVAL
     assert lib.pm_server_workspace_bytes(None, api.FP64) == 0
@@ -133,7 +133,7 @@ def test_server_and_batch_validation_without_gpu(lib_path):
 
     ops = (ctypes.c_void_p * 2)(None, None)
     which = (ctypes.c_int * 2)(0, 3)
-    for count, o in ((0, opts()), (5000, opts()), (2, opts(prec=7)), (2, opts(precision=api.BF16_REFINE)),
+    for count, o in ((0, opts()), (5000, opts()), (2, opts(prec=7)), (2, opts(precision=3)),
                      (2, opts(rtol=-1.0))):
         assert lib.pm_batch_create(ops, which, None, count, o, 0, ctypes.byref(out), None) == api.PM_EINVAL
     for bad in ((0, 9), (0, -2)):    # unknown per-entry preconditioners

@@ -122,10 +122,11 @@ def test_batch_result_does_not_depend_on_the_mix(prec):
     assert st_a[0].iters == st_m[3].iters
 
 
+@pytest.mark.parametrize("precision", [pm.FP32_REFINE, pm.BF16_REFINE])
 @pytest.mark.parametrize("prec", [pm.PREC_LINE, pm.PREC_IC0])
-def test_batch_mixed_precision(prec):
+def test_batch_mixed_precision(prec, precision):
     entries = ENTRIES + (MASS_ENTRIES if prec == pm.PREC_IC0 else [])
-    xs, stats, _ = run_batch(entries, prec, precision=pm.FP32_REFINE, rtol=1e-8)
+    xs, stats, _ = run_batch(entries, prec, precision=precision, rtol=1e-8)
     for (nm, w), x, st in zip(entries, xs, stats):
         b, op, ops = case(nm)
         assert st.status == pm.PM_OK
@@ -177,7 +178,7 @@ def test_batch_autotune_picks_a_shape():
 
 def test_batch_rejects_bad_options():
     op = case("box16")[1]
-    for opts in (pm.Options(prec=7), pm.Options(precision=pm.BF16_REFINE), pm.Options(rtol=0.0)):
+    for opts in (pm.Options(prec=7), pm.Options(precision=3), pm.Options(rtol=0.0)):
         with pytest.raises(pm.PMError) as ei:
             pm.Batch([op], [pm.OP_VEL_U1], opts)
         assert ei.value.status == pm.PM_EINVAL

@@ -24,7 +24,8 @@ def oracle_solve(ops, which, rhs):
 
 
 @pytest.mark.parametrize("precision,prec", [(pm.FP64, pm.PREC_LINE), (pm.FP32_REFINE, pm.PREC_LINE),
-                                            (pm.FP64, pm.PREC_IC0), (pm.FP32_REFINE, pm.PREC_IC0)])
+                                            (pm.FP64, pm.PREC_IC0), (pm.FP32_REFINE, pm.PREC_IC0),
+                                            (pm.BF16_REFINE, pm.PREC_LINE)])
 def test_staggered_admission_matches_one_shot_batch(precision, prec):
     """Same tile width and block as the one-shot batch: admitted in three waves between quanta,
     every system reproduces the batch's bits and iteration counts."""
