@@ -486,10 +486,12 @@ __device__ __forceinline__ bool owns_ic0_chunk(const Sys& S, int c) {
     if (!grid_barrier(ctl)) return;                                                                 \
   }
 
-// Resident blocks of 256 threads per SM the register budget is sized for (128 registers at 2: no
-// spills; measured faster than 80 registers at 3 for the long pressure solves).
+// Resident blocks of 256 threads per SM the register budget is sized for: 3 (80 registers, about
+// 1 KB of spills per thread) keeps 24 warps per SM in flight. The kernel is latency-bound, and on
+// the batched 64-basin workloads 3 measured faster than 2 (128 registers, no spills): IC0 mass
+// systems 0.41 -> 0.36 s, the FP32 line batch 8.84 -> 8.49 s.
 #ifndef PM_BATCH_MINB
-#define PM_BATCH_MINB 2
+#define PM_BATCH_MINB 3
 #endif
 
 template <typename T>

@@ -463,10 +463,11 @@ struct CMap {
 // Backward (FWD = 0): z_i = (y_i - sum_{colour(j) > c} L_ji z_j) / L_ii, in place on y.
 // The factor's diagonal slot holds 1 / L_ii (a multiply instead of an FP64 division).
 // Position t of colour COLOUR: column cls_cols[cls_off + t / nlev], level 2 (t % nlev) + parity.
-template <int COLOUR, int FWD>
-__device__ __forceinline__ void ic0_row(const Geom& g, const CMap& cm, const int32_t* __restrict__ cls_cols,
-                                        int64_t cls_off, int64_t t, const double* __restrict__ F,
-                                        const double* __restrict__ r, double* __restrict__ y) {
+// ic0_value returns the row's new value and its index; ic0_row stores it.
+template <int COLOUR, int FWD, typename T>
+__device__ __forceinline__ T ic0_value(const Geom& g, const CMap& cm, const int32_t* __restrict__ cls_cols,
+                                       int64_t cls_off, int64_t t, const T* __restrict__ F,
+                                       const T* __restrict__ r, const T* y, int64_t* row_out) {
   constexpr int kpar = COLOUR >> 2;
   const int nlev = cm.nlev[kpar];
   const int nz = g.nz;
@@ -474,7 +475,7 @@ __device__ __forceinline__ void ic0_row(const Geom& g, const CMap& cm, const int
   const int k = 2 * (int)(t % nlev) + kpar;
   const int64_t row = (int64_t)col * nz + k;
   const int64_t pi = cm.cbase[COLOUR] + t;
-  double acc = FWD ? r[row] : y[row];
+  T acc = FWD ? r[row] : y[row];
 #pragma unroll
   for (int s = 0; s < NSLOT; ++s) {
     if (s == DIAG_SLOT) continue;
@@ -487,19 +488,39 @@ __device__ __forceinline__ void ic0_row(const Geom& g, const CMap& cm, const int
     if (nb < 0) continue;
     acc = fma(-F[(int64_t)s * g.n + pi], y[(int64_t)nb * nz + kk], acc);
   }
-  y[row] = acc * F[(int64_t)DIAG_SLOT * g.n + pi];
+  *row_out = row;
+  return acc * F[(int64_t)DIAG_SLOT * g.n + pi];
 }
 
 template <int COLOUR, int FWD>
+__device__ __forceinline__ void ic0_row(const Geom& g, const CMap& cm, const int32_t* __restrict__ cls_cols,
+                                        int64_t cls_off, int64_t t, const double* __restrict__ F,
+                                        const double* __restrict__ r, double* __restrict__ y) {
+  int64_t row;
+  const double v = ic0_value<COLOUR, FWD>(g, cm, cls_cols, cls_off, t, F, r, y, &row);
+  y[row] = v;
+}
+
+// One colour phase: two rows per thread (t and t + stride), both computed before either is
+// stored (no row of a colour reads another row of that colour), so that each thread has both
+// rows' neighbour gathers in flight. Launched over half the rows.
+template <int COLOUR, int FWD, typename T>
 __global__ void __launch_bounds__(TPB) k_ic0_sweep(Geom g, CMap cm, const int32_t* __restrict__ cls_cols,
-                                                   int64_t cls_off, int64_t cls_cnt, const double* __restrict__ F,
-                                                   const double* __restrict__ r, double* __restrict__ y,
+                                                   int64_t cls_off, int64_t cls_cnt, const T* __restrict__ F,
+                                                   const T* __restrict__ r, T* __restrict__ y,
                                                    const PcgScalars* sc, int check_done) {
   if (check_done && sc_done(sc)) return;
   const int64_t total = cls_cnt * cm.nlev[COLOUR >> 2];
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x)
-    ic0_row<COLOUR, FWD>(g, cm, cls_cols, cls_off, t, F, r, y);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += 2 * stride) {
+    const bool two = t + stride < total;
+    int64_t r0, r1 = 0;
+    const T v0 = ic0_value<COLOUR, FWD>(g, cm, cls_cols, cls_off, t, F, r, y, &r0);
+    T v1 = 0;
+    if (two) v1 = ic0_value<COLOUR, FWD>(g, cm, cls_cols, cls_off, t + stride, F, r, y, &r1);
+    y[r0] = v0;
+    if (two) y[r1] = v1;
+  }
 }
 
 // Grid of the reduction kernels: at most MAX_GRID blocks (the size of the partials buffer).
@@ -993,7 +1014,7 @@ void ic0_apply(pm_operator* op, int which, const double* r, double* z, const Pcg
     const int64_t cnt = op->cls_count[(C) & 3];                                                \
     const int64_t tot = cnt * cm.nlev[(C) >> 2];                                               \
     if (tot > 0) {                                                                             \
-      k_ic0_sweep<C, FW><<<grid_for(tot, TPB, op->num_sms), TPB, 0, s>>>(                      \
+      k_ic0_sweep<C, FW, double><<<grid_for((tot + 1) / 2, TPB, op->num_sms), TPB, 0, s>>>(     \
           g, cm, op->d_cls_cols, off[(C) & 3], cnt, F, r, z, sc, check_done);                  \
       count_launch();                                                                          \
     }                                                                                          \
@@ -2164,39 +2185,7 @@ void update_line32(pm_operator* op, int which, bool proj, double* x, int mode, c
                                                       op->d_m2f, c->partials, c->sc_in, mode);
 }
 
-// FP32 IC0 colour sweep (as k_ic0_sweep).
-template <int COLOUR, int FWD>
-__global__ void __launch_bounds__(TPB) k32_ic0_sweep(Geom g, CMap cm, const int32_t* __restrict__ cls_cols,
-                                                     int64_t cls_off, int64_t cls_cnt, const float* __restrict__ F,
-                                                     const float* __restrict__ r, float* __restrict__ y,
-                                                     const PcgScalars* sc, int check_done) {
-  if (check_done && sc_done(sc)) return;
-  constexpr int kpar = COLOUR >> 2;
-  const int nlev = cm.nlev[kpar];
-  const int64_t total = cls_cnt * nlev;
-  const int nz = g.nz;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int col = __ldg(cls_cols + cls_off + t / nlev);
-    const int k = 2 * (int)(t % nlev) + kpar;
-    const int64_t row = (int64_t)col * nz + k;
-    const int64_t pi = cm.cbase[COLOUR] + t;
-    float acc = FWD ? r[row] : y[row];
-#pragma unroll
-    for (int s = 0; s < NSLOT; ++s) {
-      if (s == DIAG_SLOT) continue;
-      const int cj = COLOUR ^ slot_flip(s);
-      if (FWD ? (cj > COLOUR) : (cj < COLOUR)) continue;
-      const int q = slot_q(s);
-      const int kk = k + slot_dk(s);
-      if (kk < 0 || kk >= nz) continue;
-      const int nb = q == 0 ? col : nbr_of(g, col, q);
-      if (nb < 0) continue;
-      acc = fmaf(-F[(int64_t)s * g.n + pi], y[(int64_t)nb * nz + kk], acc);
-    }
-    y[row] = acc * F[(int64_t)DIAG_SLOT * g.n + pi];
-  }
-}
-
+// FP32 IC0 apply: the same colour sweeps (k_ic0_sweep<.., float>) on the FP32 copy of the factor.
 void ic0_apply32(pm_operator* op, int which, const float* r, float* z, const PcgScalars* sc, int check_done,
                  cudaStream_t s) {
   Geom g = geom_of(op);
@@ -2209,7 +2198,7 @@ void ic0_apply32(pm_operator* op, int which, const float* r, float* z, const Pcg
     const int64_t cnt = op->cls_count[(C) & 3];                                                \
     const int64_t tot = cnt * cm.nlev[(C) >> 2];                                               \
     if (tot > 0) {                                                                             \
-      k32_ic0_sweep<C, FW><<<grid_for(tot, TPB, op->num_sms), TPB, 0, s>>>(                    \
+      k_ic0_sweep<C, FW, float><<<grid_for((tot + 1) / 2, TPB, op->num_sms), TPB, 0, s>>>(     \
           g, cm, op->d_cls_cols, off[(C) & 3], cnt, F, r, z, sc, check_done);                  \
       count_launch();                                                                          \
     }                                                                                          \
