@@ -251,3 +251,28 @@ def test_a_request_needing_every_slot_is_served():
     # with four slots and four right-hand sides per request, requests never overlap
     recs = sorted(rep.records, key=lambda r: r.t_admit)
     assert all(b.t_admit >= a.t_done for a, b in zip(recs, recs[1:]))
+
+
+def test_request_stream_right_hand_side_counts():
+    """max_rhs = 7 (the consistent-mass correction's seven systems per step) draws 1..7 right-hand
+    sides per request; the default keeps 1..4. Only the counts depend on max_rhs: arrivals and
+    sessions are the same seeded stream."""
+    _, reqs4 = stream(n=400)
+    _, reqs7 = request_stream(seed=5, rate=200.0, n_requests=400, concurrent_sessions=8, steps_per_session=20,
+                              median_nodes=2e4, sigma=0.8, max_nodes=2e5, max_rhs=7)
+    n4 = [r.nrhs for r in reqs4]
+    n7 = [r.nrhs for r in reqs7]
+    assert set(n4) == {1, 2, 3, 4} and set(n7) == set(range(1, 8))
+    assert [(r.t_arrival, r.session, r.step) for r in reqs4] == [(r.t_arrival, r.session, r.step) for r in reqs7]
+
+
+def test_scheduler_serves_seven_system_requests():
+    """Requests of up to seven systems go through the same loop: every system admitted once, a
+    request completes when all its systems have."""
+    sess, reqs = request_stream(seed=9, rate=200.0, n_requests=120, concurrent_sessions=6, steps_per_session=20,
+                                median_nodes=2e4, sigma=0.8, max_nodes=2e5, max_rhs=7)
+    be = FakeBackend(sess, slots=16)
+    rep = Scheduler(be, sess, reqs, slots=16, quantum=8).run()
+    assert all(not math.isnan(r.t_done) for r in rep.records)
+    assert be.max_active <= 16
+    assert sum(r.nrhs for r in rep.records) == rep.solves
