@@ -55,7 +55,7 @@ class StepOptions:
     vel_rtol: float = 1e-8
     pres_rtol: float = 1e-8
     vel_prec: str = "ic0"          # "ic0" (multicolour), "ic0_natural", "jacobi"
-    pres_prec: str = "jacobi"      # "jacobi" (DIAG), "ic0"
+    pres_prec: str = "jacobi"      # "jacobi" (DIAG), "ic0", "line"
     lumped_correction: bool = True
     mass_prec: str = "ic0"
     max_iter: int = 200000
