@@ -1415,8 +1415,9 @@ extern "C" int pm_pcg_solve_batched(pm_operator* const* ops, const pm_which* whi
 // workspace. Systems are admitted and retired between launches of the persistent kernel: a new
 // system is initialised at the start of the next launch (state NEW) while the others keep their
 // state; a finished one (DONE) frees its slot and its tile range. The kernel takes the whole slot
-// table (empty slots are DONE and cost nothing) and the tile array's capacity as its partial
-// stride, so the captured graph stays valid until the tile array has to grow.
+// table (empty slots are DONE and cost nothing) and the tile capacity (the stride of the partials
+// buffer) as arguments, so the captured graph stays valid until that capacity has to grow. Each
+// system owns a range of tile indices [tile0, tile0 + ntiles): its partials' slots.
 
 struct pm_server {
   int32_t cap = 0, nz_cap = 0;
@@ -1470,7 +1471,7 @@ int server_grow_tiles(pm_server* sv, int64_t want) {
   if (want <= sv->tcap) return PM_OK;
   int64_t nc = std::max<int64_t>(sv->tcap * 2, 1024);
   while (nc < want) nc *= 2;
-  if (nc > (int64_t)1 << 30) return set_error(PM_ENOMEM, "server tile array too large");
+  if (nc > (int64_t)1 << 30) return set_error(PM_ENOMEM, "server tile capacity too large");
   double* np = nullptr;
   const int st = cuda_check(cudaMalloc((void**)&np, (size_t)NP * nc * sizeof(double)), "server partials");
   if (st) return st;
