@@ -106,8 +106,9 @@ enum { PM_PREC_JACOBI = 0, PM_PREC_IC0 = 1, PM_PREC_NONE = 2, PM_PREC_LINE = 3 }
 /* In per-entry preconditioner arguments (batches, server admission): use the options' choice. */
 #define PM_PREC_DEFAULT (-1)
 /* Arithmetic of the inner iteration. FP64 throughout, or FP32 (BF16) operator values with FP32
- * vectors inside PCG, FP64 dot products / alpha / beta, and FP64 outer iterative refinement on
- * the true residual until rtol is met. */
+ * vectors inside PCG, dot products accumulated per thread in compensated FP32 (two floats, about
+ * 48 significant bits) and reduced in FP64, FP64 alpha / beta, and FP64 outer iterative
+ * refinement on the true residual until rtol is met. */
 enum { PM_FP64 = 0, PM_FP32_REFINE = 1, PM_BF16_REFINE = 2 };
 
 typedef struct pm_solve_opts {
