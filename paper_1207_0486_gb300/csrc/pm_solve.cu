@@ -847,9 +847,8 @@ __global__ void __launch_bounds__(LINE_WTPB, TCOLS == 32 ? 3 : 4) k_update_line_
 // Columns per task: 32, so that every lane of a warp sweeps a column (an FP64 instruction costs the
 // FP64 pipe the same with idle lanes, and the sweep is a third of the kernel's FP64 work), unless
 // that leaves fewer tasks than resident warps (basins under about 600 x 600 columns of 32 levels):
-// then 16, twice the warps and half the lanes sweeping.
-constexpr int LINE_WCOLS = 32;
-
+// then 16, twice the warps and half the lanes sweeping. line_w_slots gives the resident tasks of
+// one choice.
 template <int TC>
 int line_w_slots(const void* kernel, int num_sms) {
   const size_t smem = (size_t)(LINE_WTPB / 32) * TC * (LINE_WNZ + 1) * sizeof(double);
@@ -2135,7 +2134,7 @@ __global__ void __launch_bounds__(LINE_WTPB, 4) k32_update_line_w(Geom g, const 
 
 // The FP32 fused update + line solve (mode as k32_update_line): warp tasks for 32-level columns,
 // the block kernel otherwise. One launch; the caller counts it.
-void update_line32(pm_operator* op, int which, bool proj, double* x, int mode, cudaStream_t s) {
+void update_line32(pm_operator* op, int which, bool proj, int mode, cudaStream_t s) {
   SolveCtx* c = op->ctx;
   Geom g = geom_of(op);
   if (op->nz == LINE_WNZ) {
@@ -2292,7 +2291,7 @@ double bytes_per_inner(const pm_operator* op, int prec, int vbytes, bool proj) {
 }
 
 template <int MASKC, typename TV>
-void inner_iter(pm_operator* op, int which, const TV* val32, bool proj, int prec, const float* dinv32, double* x,
+void inner_iter(pm_operator* op, int which, const TV* val32, bool proj, int prec, const float* dinv32,
                 cudaStream_t s) {
   SolveCtx* c = op->ctx;
   Geom g = geom_of(op);
@@ -2305,7 +2304,7 @@ void inner_iter(pm_operator* op, int which, const TV* val32, bool proj, int prec
   if (prec == PM_PREC_LINE) {
     {
       KtScope t(PM_KT_LINE, 1, s);
-      update_line32(op, which, proj, x, 1, s);
+      update_line32(op, which, proj, 1, s);
     }
     {
       KtScope t(PM_KT_PUPDATE, 1, s);
@@ -2343,12 +2342,11 @@ void inner_iter(pm_operator* op, int which, const TV* val32, bool proj, int prec
 }
 
 // z = P^{-1} r32, rho = (r, z'), beta = 0, p = z': the first step of an inner solve.
-void inner_first(pm_operator* op, int which, bool proj, int prec, const float* dinv32, double* x, cudaStream_t s) {
+void inner_first(pm_operator* op, int which, bool proj, int prec, const float* dinv32, cudaStream_t s) {
   SolveCtx* c = op->ctx;
-  Geom g = geom_of(op);
   const int G = grid_for(op->n, TPB, op->num_sms);
   if (prec == PM_PREC_LINE) {
-    update_line32(op, which, proj, x, 0, s);
+    update_line32(op, which, proj, 0, s);
     k32_pupd<1><<<G, TPB, 0, s>>>(op->n, c->r32, dinv32, c->z32, c->p32, c->sc_in, 1);
   } else if (prec == PM_PREC_IC0) {
     ic0_apply32(op, which, c->r32, c->z32, c->sc_in, 0, s);
@@ -2440,7 +2438,7 @@ int mixed_run(pm_operator* op, int which, const double* b, double* x, const pm_s
     k32_from64<<<G, TPB, 0, s>>>(op->n, c->r, c->r32);
     count_launch();
     if ((st = cuda_check(cudaMemsetAsync(c->d32, 0, (size_t)op->n * sizeof(float), s), "d32"))) return st;
-    inner_first(op, which, proj, prec, dinv32, x, s);
+    inner_first(op, which, proj, prec, dinv32, s);
     if ((st = read_inner(c, s))) return st;
     int64_t issued = 0;
     const int32_t zero = 0;
@@ -2450,7 +2448,7 @@ int mixed_run(pm_operator* op, int which, const double* b, double* x, const pm_s
       int chunk = 4;
       while (!c->sc_in_host->done) {
         if (issued > (int64_t)o->max_iter + 4096) return set_error(PM_ECUDA, "mixed PCG: device never reported completion");
-        for (int it = 0; it < chunk; ++it) inner_iter<MASKC, TV>(op, which, val32, proj, prec, dinv32, x, s);
+        for (int it = 0; it < chunk; ++it) inner_iter<MASKC, TV>(op, which, val32, proj, prec, dinv32, s);
         issued += chunk;
         if ((st = read_inner(c, s))) return st;
         if (chunk < 64) chunk *= 2;
@@ -2490,7 +2488,7 @@ int mixed_run(pm_operator* op, int which, const double* b, double* x, const pm_s
         return st;
       k32_from64<<<G, TPB, 0, s>>>(op->n, c->r, c->r32);
       count_launch();
-      inner_first(op, which, proj, prec, dinv32, x, s);
+      inner_first(op, which, proj, prec, dinv32, s);
       if ((st = read_inner(c, s))) return st;
     }
     inner_total = c->sc_in_host->iter;
