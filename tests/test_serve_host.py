@@ -24,7 +24,7 @@ class FakeBackend:
     needs iters(key) iterations; a serial solve costs its iterations x (t_iter_serial)."""
 
     def __init__(self, sessions, slots, total_bytes=1 << 40, t_launch=2e-4, t_row=2e-10, t_iter_serial=4e-5,
-                 fail_at_quantum=None):
+                 fail_at_quantum=None, bad_keys=()):
         self.sessions = sessions
         self.slots = slots
         self.t = 0.0
@@ -36,6 +36,7 @@ class FakeBackend:
         self.max_active = 0
         self.quanta = 0
         self.fail_at = fail_at_quantum
+        self.bad = set(bad_keys)     # systems whose solve ends in breakdown (e.g. a NaN right-hand side)
         self.closed = []
         self.peak_used = 0
 
@@ -90,7 +91,8 @@ class FakeBackend:
         return sum(1 for v in self.active.values() if v[1] > 0)
 
     def poll(self):
-        out = [(s, Stats(self.iters(v[0]))) for s, v in self.active.items() if v[1] == 0]
+        out = [(s, Stats(self.iters(v[0]), status=5 if v[0] in self.bad else 0))
+               for s, v in self.active.items() if v[1] == 0]
         for s, _ in out:
             del self.active[s]
         return out
@@ -276,3 +278,18 @@ def test_scheduler_serves_seven_system_requests():
     assert all(not math.isnan(r.t_done) for r in rep.records)
     assert be.max_active <= 16
     assert sum(r.nrhs for r in rep.records) == rep.solves
+
+
+def test_a_failed_system_fails_only_its_request():
+    """A system that ends in breakdown (a NaN right-hand side, injected on the host) marks its own
+    request's status and nothing else: every other request completes with PM_OK, and the report
+    counts one failed solve."""
+    sess, reqs = stream(n=120)
+    bad = (7, 0)
+    be = FakeBackend(sess, slots=16, bad_keys=[bad])
+    rep = Scheduler(be, sess, reqs, slots=16, quantum=8).run()
+    assert all(not math.isnan(r.t_done) for r in rep.records)
+    for r in rep.records:
+        want = [5 if (r.index, j) == bad else 0 for j in range(r.nrhs)]
+        assert r.status == want, (r.index, r.status)
+    assert rep.summary()["failed_solves"] == 1
