@@ -45,6 +45,7 @@ class RequestRecord:
     iters: List[int] = field(default_factory=list)
     status: List[int] = field(default_factory=list)
     rel_residual: List[float] = field(default_factory=list)
+    cancelled: bool = False      # withdrawn by its client before it was admitted
 
     @property
     def latency(self) -> float:
@@ -83,6 +84,7 @@ class ServeReport:
             "max_ms": float(lat.max()) if lat.size else None,
             "makespan_s": self.makespan,
             "failed_solves": bad,
+            "cancelled_requests": sum(1 for r in self.records if r.cancelled),
             "mean_iters": float(np.mean(its)) if its else 0.0,
             "sessions": self.sessions_opened,
             "peak_resident_sessions": self.peak_resident_sessions,
@@ -101,10 +103,14 @@ class Scheduler:
         run(quantum) -> systems still active;  poll() -> [(slot, stats)]
         solve_now(handle, j, rhs_seed, key) -> stats          (serial mode)
     stats: objects with .iters, .status, .rel_residual_true.
+    cancel: optional {request index: time} at which the request's client withdraws it (on the
+    requests' clock). A request still queued then is dropped (record.cancelled); one already
+    admitted runs to completion, since its systems are already on the GPU. A session closes once
+    none of its requests is outstanding.
     """
 
     def __init__(self, backend, sessions: Sequence, requests: Sequence, slots: int = 64, quantum: int = 16,
-                 reserve_bytes: int = 1 << 30, mode: str = "continuous"):
+                 reserve_bytes: int = 1 << 30, mode: str = "continuous", cancel: Optional[Dict[int, float]] = None):
         if mode not in ("continuous", "serial"):
             raise ValueError("mode must be 'continuous' or 'serial'")
         self.be = backend
@@ -114,9 +120,7 @@ class Scheduler:
         self.quantum = quantum
         self.reserve = reserve_bytes
         self.mode = mode
-        self.last_step: Dict[int, int] = {}
-        for r in self.requests:
-            self.last_step[r.session] = max(self.last_step.get(r.session, -1), r.step)
+        self.cancel = dict(cancel or {})
 
     def run(self) -> ServeReport:
         be = self.be
@@ -134,6 +138,14 @@ class Scheduler:
         need_of: Dict[int, int] = {}       # session -> device bytes it needs when opened
         t0 = be.now()
         first_arrival = recs[order[0]].t_arrival if recs else 0.0
+        outstanding: Dict[int, int] = {}   # session -> requests neither finished nor cancelled
+        for r in recs:
+            outstanding[r.session] = outstanding.get(r.session, 0) + 1
+
+        def resolve(rec):
+            outstanding[rec.session] -= 1
+            if outstanding[rec.session] == 0 and rec.session in open_h and rec.session not in busy:
+                be.close_session(open_h.pop(rec.session))
 
         def finish(ri, t):
             nonlocal done
@@ -141,8 +153,15 @@ class Scheduler:
             rec.t_done = t
             done += 1
             del busy[rec.session]
-            if rec.step >= self.last_step[rec.session]:
-                be.close_session(open_h.pop(rec.session))
+            resolve(rec)
+
+        def drop_cancelled(t):
+            nonlocal done
+            for ri in [i for i in queue if self.cancel.get(i, math.inf) <= t]:
+                queue.remove(ri)
+                recs[ri].cancelled = True
+                done += 1
+                resolve(recs[ri])
 
         def ensure_open(rec) -> bool:
             nonlocal opened, peak
@@ -163,6 +182,7 @@ class Scheduler:
             while nxt < len(order) and recs[order[nxt]].t_arrival <= t:
                 queue.append(order[nxt])
                 nxt += 1
+            drop_cancelled(t)
             if self.mode == "serial":
                 if not queue:
                     be.sleep(max(0.0, recs[order[nxt]].t_arrival - (be.now() - t0)))
@@ -221,6 +241,8 @@ class Scheduler:
                         finish(ri, tq)
             elif nxt < len(order):
                 be.sleep(max(0.0, recs[order[nxt]].t_arrival - (be.now() - t0)))
+            elif queue and any(i in self.cancel for i in queue):
+                be.sleep(max(0.0, min(self.cancel[i] for i in queue if i in self.cancel) - (be.now() - t0)))
             elif queue:
                 raise RuntimeError("queued requests can never be admitted (slots or memory too small)")
         last = max((r.t_done for r in recs), default=0.0)

@@ -37,6 +37,7 @@ class FakeBackend:
         self.quanta = 0
         self.fail_at = fail_at_quantum
         self.bad = set(bad_keys)     # systems whose solve ends in breakdown (e.g. a NaN right-hand side)
+        self.admitted = []
         self.closed = []
         self.peak_used = 0
 
@@ -75,6 +76,7 @@ class FakeBackend:
             return None
         free = [s for s in range(self.slots) if s not in self.active]
         s = free[0]
+        self.admitted.append(key)
         self.active[s] = [key, self.iters(key), self.rows(self.sessions[self.open[h]])]
         self.max_active = max(self.max_active, len(self.active))
         return s
@@ -98,6 +100,7 @@ class FakeBackend:
         return out
 
     def solve_now(self, h, j, seed, key):
+        self.admitted.append(key)
         it = self.iters(key)
         self.t += it * self.t_iter_serial
         return Stats(it)
@@ -293,3 +296,30 @@ def test_a_failed_system_fails_only_its_request():
         want = [5 if (r.index, j) == bad else 0 for j in range(r.nrhs)]
         assert r.status == want, (r.index, r.status)
     assert rep.summary()["failed_solves"] == 1
+
+
+@pytest.mark.parametrize("mode", ["continuous", "serial"])
+def test_cancelled_requests_are_dropped_before_admission(mode):
+    """Clients withdraw every fifth request just after it arrives. On a congested backend (few
+    slots) those still queued are dropped: none of their systems is admitted or solved, their
+    records say cancelled, every other request completes, and every opened session is closed
+    (a session whose last step was cancelled included). A request already admitted when its
+    client cancels runs to completion."""
+    sess, reqs = stream(n=160, rate=2000.0)
+    cancel = {i: reqs[i].t_arrival + 1e-6 for i in range(0, len(reqs), 5)}
+    be = FakeBackend(sess, slots=6)
+    rep = Scheduler(be, sess, reqs, slots=6, quantum=8, mode=mode, cancel=cancel).run()
+    dropped = [r.index for r in rep.records if r.cancelled]
+    assert dropped, "the backend was not congested enough for any cancellation to land"
+    assert set(dropped) <= set(cancel)
+    for r in rep.records:
+        if r.cancelled:
+            assert math.isnan(r.t_done) and not r.iters
+            assert not any(k[0] == r.index for k in be.admitted)
+        else:
+            assert not math.isnan(r.t_done) and len(r.iters) == r.nrhs
+    # cancellations that came after admission did not stop those requests
+    assert any(i in cancel and not rep.records[i].cancelled for i in range(len(reqs)))
+    assert not be.open, "a session stayed open"
+    assert rep.summary()["cancelled_requests"] == len(dropped)
+    assert rep.solves == sum(r.nrhs for r in rep.records if not r.cancelled)
