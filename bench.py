@@ -326,15 +326,19 @@ def run_small_leg():
     solves/s, not as a fraction of HBM. One solve per call to 1e-10 (FP64) or 1e-8 (mixed) from
     x = 0, seeded N(0, 1) right-hand sides; velocity u1 with IC0, pressure with the line
     preconditioner and with Jacobi. The mixed-precision rows are the same geometry with FP32 / BF16
-    operator values (FP64 dots and refinement), with their error against the FP64 solution."""
+    operator values (FP64 dots and refinement), with their error against the FP64 solution. The
+    mms_* rows solve right-hand sides manufactured from a smooth seeded field u* (b = A u*, the
+    small configuration's form) and report the error against u*."""
     import torch
     import paper_1207_0486_gb300 as pm
-    from workloads import box_basin
+    from workloads import box_basin, manufactured_field, mms_modes
 
-    op = pm.assemble_operator(box_basin())
+    basin = box_basin()
+    op = pm.assemble_operator(basin)
     gen = torch.Generator(device="cuda")
     gen.manual_seed(1207)
-    out = {"workload": "box 16x16x8 (2,048 nodes), x0 = 0, seeded N(0, 1) right-hand side"}
+    out = {"workload": "box 16x16x8 (2,048 nodes), x0 = 0, seeded N(0, 1) right-hand side; mms_* rows: "
+                       "b = A u* for the seeded sinusoid field u* (workloads.manufactured_field)"}
     cases = [(pm.OP_VEL_U1, "velocity_ic0", pm.PREC_IC0, pm.FP64, 1e-10),
              (pm.OP_PRESSURE, "pressure_line", pm.PREC_LINE, pm.FP64, 1e-10),
              (pm.OP_PRESSURE, "pressure_jacobi", pm.PREC_JACOBI, pm.FP64, 1e-10),
@@ -367,6 +371,30 @@ def run_small_leg():
             row["rel_err_vs_fp64"] = float(f"{float((x - r).norm() / r.norm()):.3e}")
             row["outer_iters"] = int(st.outer_iters)
         out[label] = row
+    # manufactured right-hand sides: b = A u*, so the exact solution is u* (the pressure's is u*
+    # minus its M-weighted mean, m = M 1)
+    ci, cj = op.columns()
+    us = torch.from_numpy(manufactured_field(basin, ci, cj, mms_modes())).cuda()
+    m = torch.zeros_like(us)
+    op.spmv(pm.OP_MASS, torch.ones_like(us), m)
+    for which, label, prec in ((pm.OP_VEL_U1, "mms_velocity_ic0", pm.PREC_IC0),
+                               (pm.OP_PRESSURE, "mms_pressure_line", pm.PREC_LINE)):
+        b = torch.zeros_like(us)
+        op.spmv(which, us, b)
+        exact = us - (m @ us) / m.sum() if which == pm.OP_PRESSURE else us
+        x = torch.zeros_like(us)
+        opts = pm.Options(rtol=1e-10, prec=prec, max_iter=100000)
+        op.solve(which, b, x, opts)
+        torch.cuda.synchronize()
+        reps = 50
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            x.zero_()
+            st = op.solve(which, b, x, opts)
+        dt = (time.perf_counter() - t0) / reps
+        out[label] = {"us_per_solve": round(dt * 1e6, 1), "solves_per_s": round(1.0 / dt, 1), "iters": int(st.iters),
+                      "rel_residual_true": float(f"{st.rel_residual_true:.3e}"),
+                      "rel_err_vs_manufactured": float(f"{float((x - exact).norm() / exact.norm()):.3e}")}
     op.close()
     return out
 

@@ -14,5 +14,6 @@ from .basins import (  # noqa: F401
     Session,
     Request,
     mms_modes,
+    manufactured_field,
     random_vector,
 )

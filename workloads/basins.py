@@ -237,6 +237,24 @@ def mms_modes(seed: int = 1207, count: int = 4):
     return [(float(amps[q]), int(ms[q]), int(ls[q])) for q in range(count)]
 
 
+def manufactured_field(basin: Basin, col_i: np.ndarray, col_j: np.ndarray, modes) -> np.ndarray:
+    """A smooth field sampled at the nodes of the given columns (node = column * nz + k, the
+    library's and the oracle's order), for manufactured right-hand sides b = A u*:
+        u*(x, y, z) = sum_q a_q sin(m_q pi x / Lx) sin(l_q pi y / Ly) cos(pi s / 2),
+    s = -z / h in [0, 1] the depth fraction (1 at the sea floor, 0 at the surface), with the
+    modes (a_q, m_q, l_q) of mms_modes. Grid geometry only: x = i dx, y = j dy,
+    z_k = -h (1 - k / (nz - 1))."""
+    col_i = np.asarray(col_i)
+    col_j = np.asarray(col_j)
+    x = col_i * basin.dx / max(basin.Lx, 1e-300)
+    y = col_j * basin.dy / max(basin.Ly, 1e-300)
+    s = 1.0 - np.arange(basin.nz) / (basin.nz - 1)
+    horiz = np.zeros(len(col_i))
+    for a, m, l in modes:
+        horiz += a * np.sin(m * math.pi * x) * np.sin(l * math.pi * y)
+    return (horiz[:, None] * np.cos(0.5 * math.pi * s)[None, :]).ravel()
+
+
 def random_vector(n: int, seed: int) -> np.ndarray:
     """Seeded N(0, 1) float64 vector of length n."""
     return np.random.default_rng(seed).standard_normal(n)
