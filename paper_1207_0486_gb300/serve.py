@@ -98,7 +98,8 @@ class Scheduler:
     """The request loop. backend: object with
         now() -> seconds;  sleep(seconds)
         free_bytes() -> int;  session_bytes(session) -> int
-        open_session(session_id, session) -> handle;  close_session(handle)
+        open_session(session_id, session) -> handle (raises MemoryError when the device cannot hold
+            the session now);  close_session(handle)
         admit(handle, j, rhs_seed, key) -> slot or None (no free slot)
         run(quantum) -> systems still active;  poll() -> [(slot, stats)]
         solve_now(handle, j, rhs_seed, key) -> stats          (serial mode)
@@ -172,7 +173,14 @@ class Scheduler:
             if be.free_bytes() - need_of[rec.session] < self.reserve:
                 deferred.add(rec.index)
                 return False
-            open_h[rec.session] = be.open_session(rec.session, self.sessions[rec.session])
+            try:
+                open_h[rec.session] = be.open_session(rec.session, self.sessions[rec.session])
+            except MemoryError:
+                # the estimate said it fits, the allocation said no: wait as for memory, and ask
+                # for more headroom next time
+                need_of[rec.session] *= 2
+                deferred.add(rec.index)
+                return False
             opened += 1
             peak = max(peak, len(open_h))
             return True
@@ -330,14 +338,25 @@ class GpuBackend:
         return h
 
     def _open(self, sid, session):
+        """Operators and per-system vectors of one session; MemoryError (nothing kept) when the
+        device runs out during assembly or allocation."""
         torch = self.torch
-        op = self.api.assemble_operator(self._basin(session))
+        try:
+            op = self.api.assemble_operator(self._basin(session))
+        except self.api.PMError as ex:
+            if ex.status == self.api.PM_ENOMEM:
+                raise MemoryError(str(ex)) from ex
+            raise
         n = op.n
-        ws = int(self.api.load().pm_server_workspace_bytes(self.api._handle(op.handle), self.opts.precision))
-        h = {"sid": sid, "op": op,
-             "x": [torch.zeros(n, dtype=torch.float64, device="cuda") for _ in self.which],
-             "b": [torch.empty(n, dtype=torch.float64, device="cuda") for _ in self.which],
-             "work": [torch.empty(ws, dtype=torch.uint8, device="cuda") for _ in self.which]}
+        try:
+            ws = int(self.api.load().pm_server_workspace_bytes(self.api._handle(op.handle), self.opts.precision))
+            h = {"sid": sid, "op": op,
+                 "x": [torch.zeros(n, dtype=torch.float64, device="cuda") for _ in self.which],
+                 "b": [torch.empty(n, dtype=torch.float64, device="cuda") for _ in self.which],
+                 "work": [torch.empty(ws, dtype=torch.uint8, device="cuda") for _ in self.which]}
+        except torch.cuda.OutOfMemoryError as ex:
+            op.close()
+            raise MemoryError(str(ex)) from ex
         return h
 
     def close_session(self, h):

@@ -24,7 +24,7 @@ class FakeBackend:
     needs iters(key) iterations; a serial solve costs its iterations x (t_iter_serial)."""
 
     def __init__(self, sessions, slots, total_bytes=1 << 40, t_launch=2e-4, t_row=2e-10, t_iter_serial=4e-5,
-                 fail_at_quantum=None, bad_keys=()):
+                 fail_at_quantum=None, bad_keys=(), oom_opens=0):
         self.sessions = sessions
         self.slots = slots
         self.t = 0.0
@@ -38,6 +38,7 @@ class FakeBackend:
         self.fail_at = fail_at_quantum
         self.bad = set(bad_keys)     # systems whose solve ends in breakdown (e.g. a NaN right-hand side)
         self.admitted = []
+        self.oom_opens = oom_opens   # the first session openings fail with MemoryError (injected)
         self.closed = []
         self.peak_used = 0
 
@@ -62,6 +63,9 @@ class FakeBackend:
         return self.total - sum(self.session_bytes(self.sessions[h]) for h in self.open.values())
 
     def open_session(self, sid, s):
+        if self.oom_opens > 0:
+            self.oom_opens -= 1
+            raise MemoryError("device allocation failed (injected)")
         h = len(self.open) + 1000 * (1 + len(self.closed))
         self.open[h] = sid
         self.peak_used = max(self.peak_used, self.total - self.free_bytes())
@@ -323,3 +327,16 @@ def test_cancelled_requests_are_dropped_before_admission(mode):
     assert not be.open, "a session stayed open"
     assert rep.summary()["cancelled_requests"] == len(dropped)
     assert rep.solves == sum(r.nrhs for r in rep.records if not r.cancelled)
+
+
+def test_an_allocation_failure_when_opening_a_session_defers_it():
+    """Three session openings fail with an out-of-memory error although the estimate said they fit
+    (injected on the host): the requests wait as for memory and are served once an opening
+    succeeds; nothing is lost and every session is closed at the end."""
+    sess, reqs = stream(n=80)
+    be = FakeBackend(sess, slots=16, oom_opens=3)
+    rep = Scheduler(be, sess, reqs, slots=16, quantum=8).run()
+    assert be.oom_opens == 0
+    assert all(not math.isnan(r.t_done) for r in rep.records)
+    assert rep.summary()["deferred_for_memory"] >= 1
+    assert not be.open
